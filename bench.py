@@ -1,0 +1,352 @@
+"""Benchmark: pack + unpack of the six halo faces of a 512^3 float64 grid.
+
+One step = pack the six send faces (a struct of six subarray types, one
+kernel launch) into one contiguous 24 MiB buffer, then unpack that buffer
+into the same six faces of a second 512^3 grid (one launch per face: the
+faces share edge cells, so together they are an overlapping receive layout,
+while each face alone is not).  Metric:
+algorithmic bytes (read + written user bytes, 2 * packed bytes per pack and
+per unpack) per second.  L2 is flushed between timed steps (a 512 MiB write
+outside the timed events), since the touched bytes would otherwise fit in
+the 126 MB L2.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dte|reference]
+
+--impl reference times the CPU oracle (the plain typemap walker) on the same
+workload (a bounded sample of steps) and prints the same JSON line with
+"impl": "reference".  Under torchrun each rank runs the workload on its own
+GPU (independent replicas, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+N = 512
+G = 2
+ALG_FACTOR = 2  # read + write per moved byte
+METRIC = "pack+unpack GB/s (algorithmic bytes, % of HBM roofline)"
+WORKLOAD = "512^3 float64 grid, six halo faces (ghost 2): pack all six into one buffer, unpack into a second grid"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="dte", choices=["dte", "reference"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def csrc_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2402_12274_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        with open(os.path.join(d, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except OSError:
+        return None
+    ent = rec.get(kernel)
+    if not ent or ent.get("csrc_hash") != csrc_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_steps(seconds_budget: float, max_steps: int | None = None):
+    """Time the oracle on the same pack+unpack step; returns (GB/s, steps, secs)."""
+    import oracle
+    from paper_2402_12274_gb300 import inputs
+    faces = [oracle.from_spec(f) for f in inputs.halo_face_specs(N, G)]
+    send = oracle.from_spec(inputs.all_faces_struct(inputs.halo_face_specs(N, G)))
+    grid = np.zeros(N ** 3, np.float64)
+    grid[:] = inputs.normal_f64(N ** 3, 2)
+    g2 = np.zeros_like(grid)
+    size = send.size
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        pk = send.pack(grid.view(np.uint8), 1)
+        pos = 0
+        for f in faces:
+            f.unpack(pk[pos:pos + f.size], 1, g2.view(np.uint8))
+            pos += f.size
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds_budget or (max_steps and steps >= max_steps):
+            break
+    alg = 2 * ALG_FACTOR * size * steps
+    return alg / el / 1e9, steps, el
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    budget = min(60.0, 2.0 * (args.steps + args.warmup))
+    gbs, steps, el = oracle_steps(budget, max_steps=args.steps)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(gbs, 4), "unit": "GB/s", "n_gpus": world,
+        "steps": steps, "warmup": 0, "ms_per_step": round(1e3 * el / steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"{steps} full steps"},
+        "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{steps} full pack+unpack steps, single thread"},
+        "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+def run_dte(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2402_12274_gb300 as dte
+    from paper_2402_12274_gb300 import inputs
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    send = dte.Datatype.from_spec(inputs.all_faces_struct(inputs.halo_face_specs(N, G))).commit()
+    faces = [dte.Datatype.from_spec(f).commit() for f in inputs.halo_face_specs(N, G)]
+    size = send.size
+    fsz = [f.size for f in faces]
+    offs = np.concatenate([[0], np.cumsum(fsz)[:-1]]).tolist()
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(2)
+    grid = torch.randn(N ** 3, dtype=torch.float64, device=dev, generator=gen)
+    grid2 = torch.zeros_like(grid)
+    packed = torch.empty(size, dtype=torch.uint8, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    sh = stream.cuda_stream
+
+    def unpack_all(dst):
+        for f, o in zip(faces, offs):
+            dte.dte_unpack_enqueue(packed.data_ptr(), size, o, dst, 1, f.h, sh)
+
+    def step():
+        dte.dte_pack_enqueue(grid.data_ptr(), 1, send.h, packed.data_ptr(), size, 0, sh)
+        unpack_all(grid2.data_ptr())
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            step()
+            flush.zero_()
+    stream.synchronize()
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            for i in range(K):
+                flush.zero_()
+                ev[i][0].record(stream)
+                dte.dte_pack_enqueue(grid.data_ptr(), 1, send.h, packed.data_ptr(), size, 0, sh)
+                ev[i][1].record(stream)
+                unpack_all(grid2.data_ptr())
+                ev[i][2].record(stream)
+        stream.synchronize()
+    torch.cuda.synchronize()
+    t_pack = np.array([ev[i][0].elapsed_time(ev[i][1]) for i in range(K)]) * 1e-3
+    t_unpack = np.array([ev[i][1].elapsed_time(ev[i][2]) for i in range(K)]) * 1e-3
+    total = float((t_pack + t_unpack).sum())
+    if world > 1:
+        tt = torch.tensor([total], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total = float(tt.item())
+        dist.barrier()
+    alg_step = 2 * ALG_FACTOR * size
+    value = alg_step * K * world / total / 1e9
+
+    # e2e: the same step through the C ABI on pinned host grids (the kernels
+    # read and write host memory over NVLink-C2C; no staging copies)
+    e2e = None
+    if not args.no_e2e:
+        h_grid = torch.empty(N ** 3, dtype=torch.float64, pin_memory=True)
+        h_grid.copy_(grid.cpu())
+        h_grid2 = torch.zeros(N ** 3, dtype=torch.float64, pin_memory=True)
+
+        def step_host():
+            dte.dte_pack_enqueue(h_grid.data_ptr(), 1, send.h, packed.data_ptr(), size, 0, sh)
+            unpack_all(h_grid2.data_ptr())
+
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                step_host()
+        stream.synchronize()
+        ke = max(5, min(K, 20))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(ke):
+                step_host()
+            e1.record(stream)
+        stream.synchronize()
+        te = e0.elapsed_time(e1) * 1e-3
+        if world > 1:
+            tt = torch.tensor([te], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": round(alg_step * ke * world / te / 1e9, 3), "unit": "GB/s",
+               "h2d_bytes_per_step": size, "d2h_bytes_per_step": size,
+               "mode": "pinned host grids accessed by the kernels (zero-copy over NVLink-C2C)"}
+
+    # correctness spot check (not timed): the second grid holds the faces
+    g3, h3 = grid.view(N, N, N), grid2.view(N, N, N)
+    ok = bool(torch.equal(h3[G:2 * G], g3[G:2 * G]) and torch.equal(h3[:, N - 2 * G:N - G], g3[:, N - 2 * G:N - G])
+              and torch.equal(h3[:, :, G:2 * G], g3[:, :, G:2 * G]))
+
+    peak, peak_kind = peaks()
+    mp, mu = float(t_pack.mean()), float(t_unpack.mean())
+    dom = "pack" if mp >= mu else "unpack"
+    # per launch: one pack launch moves `size` bytes; the unpack leg is six launches
+    tdom = mp if dom == "pack" else mu / len(faces)
+    per_launch = size if dom == "pack" else size // len(faces)
+    achieved = ALG_FACTOR * per_launch / tdom / 1e9
+    kname = "move_kernel<16,true,true>" if dom == "pack" else "move_kernel<16,false,true>"
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic_from_profile(kname),
+            "kernel": kname, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+            "pack_ms": round(mp * 1e3, 4), "unpack_ms": round(mu * 1e3, 4),
+            "alg_bytes_per_launch": ALG_FACTOR * per_launch}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        gbs, st, el = oracle_steps(12.0)
+        cpu = {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"{st} full pack+unpack steps of the same workload, {el:.1f} s, single thread"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": K,
+            "warmup": max(args.warmup, 3), "ms_per_step": round(1e3 * total / K, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "packed_bytes": size, "alg_bytes_per_step": alg_step,
+                       "l2": "flushed between steps (512 MiB write outside the timed events)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": (1 + len(faces)) * K,
+            "clocks": clk.summary(), "check": "ok" if ok else "MISMATCH",
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_dte(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,246 @@
+/*
+ * dte.h -- GB300 datatype engine: the C ABI.
+ *
+ * A derived datatype describes a memory layout (arxiv 2402.12274, §3
+ * "Derived Datatypes").  This library builds such types with MPI-style
+ * constructors, commits them into a compact device descriptor, answers the
+ * paper's segment ("iov") queries (§3.1 MPIX_Type_iov_len / MPIX_Type_iov)
+ * and packs / unpacks non-contiguous buffers with sm_103a kernels that are
+ * enqueued on a caller-supplied CUDA stream (the stream-enqueue semantics of
+ * §5: work is ordered by the stream, nothing synchronises the host).
+ *
+ * Conventions for every call below:
+ *   - Every call returns an int: DTE_SUCCESS (0) or one of DTE_ERR_*.  No
+ *     call aborts; out-parameters are written only on success.
+ *   - Counts, sizes, displacements, strides and offsets are int64_t byte
+ *     counts unless the parameter says "in extents of old".
+ *   - dte_type handles are opaque, library owned and reference counted.
+ *     Constructors return a new, uncommitted handle in *out; release it with
+ *     dte_type_free.  A constructed type keeps what it needs from its inputs,
+ *     so the inputs may be freed right after the constructor returns.
+ *     Predefined (basic) handles from dte_type_basic are never freed.
+ *   - Buffers are caller owned.  Device buffers must stay valid until the
+ *     stream has executed the enqueued operation (CUDA stream semantics).
+ *   - Streams are CUDA runtime streams (cudaStream_t); NULL is the legacy
+ *     default stream.  Enqueue calls return as soon as the work is queued.
+ *   - Thread safety: distinct handles may be used from distinct threads;
+ *     concurrent calls on one handle must be serialised by the caller.
+ */
+#ifndef DTE_H
+#define DTE_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DTE_API __attribute__((visibility("default")))
+#else
+#define DTE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;                         /* == cudaStream_t's pointee */
+typedef struct CUstream_st *dte_stream_t;   /* interchangeable with cudaStream_t */
+
+typedef struct dte_type_s *dte_type;
+
+/* One segment: a base address and a byte length.  Same layout as
+ * struct iovec and MPIX_Iov (§3.1). */
+typedef struct dte_iov {
+    void *iov_base;
+    int64_t iov_len;
+} dte_iov;
+
+enum dte_error {
+    DTE_SUCCESS = 0,
+    DTE_ERR_ARG = 1,          /* null pointer, negative count, bad enum, ... */
+    DTE_ERR_TYPE = 2,         /* freed/invalid handle, or not committed      */
+    DTE_ERR_OVERFLOW = 3,     /* a byte count or displacement exceeds int64   */
+    DTE_ERR_TRUNCATE = 4,     /* output buffer smaller than the data         */
+    DTE_ERR_OVERLAP = 5,      /* unpack target layout writes a byte twice    */
+    DTE_ERR_NOMEM = 6,        /* host or device allocation failed            */
+    DTE_ERR_CUDA = 7,         /* a CUDA runtime call failed                  */
+    DTE_ERR_TIMEOUT = 8,      /* a bounded device wait gave up               */
+    DTE_ERR_UNSUPPORTED = 9,  /* a limit of this implementation was exceeded */
+    DTE_ERR_NODEVICE = 10     /* the call needs a CUDA device and none exists */
+};
+
+/* Basic types: (size, natural alignment) in bytes. */
+enum dte_basic {
+    DTE_BYTE = 0,      /* 1, 1 */
+    DTE_INT8,          /* 1, 1 */
+    DTE_UINT8,         /* 1, 1 */
+    DTE_INT16,         /* 2, 2 */
+    DTE_UINT16,        /* 2, 2 */
+    DTE_INT32,         /* 4, 4 */
+    DTE_UINT32,        /* 4, 4 */
+    DTE_INT64,         /* 8, 8 */
+    DTE_UINT64,        /* 8, 8 */
+    DTE_FLOAT16,       /* 2, 2 (not an MPI type; moved as bytes) */
+    DTE_BFLOAT16,      /* 2, 2 (not an MPI type; moved as bytes) */
+    DTE_FLOAT32,       /* 4, 4 */
+    DTE_FLOAT64,       /* 8, 8 */
+    DTE_NBASIC
+};
+
+enum dte_order { DTE_ORDER_C = 0, DTE_ORDER_FORTRAN = 1 };
+
+/* Human-readable name of an error code (static storage, never NULL). */
+DTE_API const char *dte_error_string(int code);
+
+/* ------------------------------------------------------------------------
+ * Type constructors (§3: types nest arbitrarily, carry offsets and may
+ * overlap; the paper's example uses contiguous and subarray, §3.2).
+ * Typemap order and lb/ub follow the MPI constructor definitions; a
+ * constructed type's lb/ub is the min/max over its copies of (copy
+ * displacement + child lb/ub), where explicit bounds (resized, subarray)
+ * take precedence, and a struct without an explicit ub has its extent
+ * rounded up to its largest basic alignment.
+ * ------------------------------------------------------------------------ */
+
+/* Predefined handle for a basic type (DTE_ERR_ARG if `which` is invalid). */
+DTE_API int dte_type_basic(int which, dte_type *out);
+
+/* count copies of old, each at i * extent(old). */
+DTE_API int dte_type_contiguous(int64_t count, dte_type old, dte_type *out);
+
+/* count blocks of bl copies of old; block i starts at i*stride extents of
+ * old (stride may be negative or zero). */
+DTE_API int dte_type_vector(int64_t count, int64_t bl, int64_t stride, dte_type old, dte_type *out);
+
+/* as vector, but stride_bytes is a byte stride. */
+DTE_API int dte_type_hvector(int64_t count, int64_t bl, int64_t stride_bytes, dte_type old, dte_type *out);
+
+/* count blocks; block i is bl[i] copies of old starting at disp[i] extents
+ * of old.  bl[] and disp[] are host arrays of `count` entries, read during
+ * the call only. */
+DTE_API int dte_type_indexed(int64_t count, const int64_t *bl, const int64_t *disp,
+                     dte_type old, dte_type *out);
+
+/* as indexed, with byte displacements. */
+DTE_API int dte_type_hindexed(int64_t count, const int64_t *bl, const int64_t *disp_bytes,
+                      dte_type old, dte_type *out);
+
+/* as indexed with every block length equal to bl. */
+DTE_API int dte_type_indexed_block(int64_t count, int64_t bl, const int64_t *disp,
+                           dte_type old, dte_type *out);
+
+/* as hindexed with every block length equal to bl. */
+DTE_API int dte_type_hindexed_block(int64_t count, int64_t bl, const int64_t *disp_bytes,
+                            dte_type old, dte_type *out);
+
+/* count blocks; block i is bl[i] copies of types[i] at byte disp[i]. */
+DTE_API int dte_type_struct(int64_t count, const int64_t *bl, const int64_t *disp_bytes,
+                    const dte_type *types, dte_type *out);
+
+/* An ndims-dimensional sub-block (subsizes at starts) of a full array
+ * (sizes) of old, in C (last index fastest) or Fortran order; lb = 0 and
+ * extent = prod(sizes) * extent(old).  ndims <= 32. */
+DTE_API int dte_type_subarray(int ndims, const int64_t *sizes, const int64_t *subsizes,
+                      const int64_t *starts, int order, dte_type old, dte_type *out);
+
+/* Same typemap as old with lb and extent replaced. */
+DTE_API int dte_type_resized(dte_type old, int64_t lb, int64_t extent, dte_type *out);
+
+/* A new handle for the same type (committed if old is). */
+DTE_API int dte_type_dup(dte_type old, dte_type *out);
+
+/* Commit: lower the type into its device descriptor (merged contiguous runs,
+ * per-level counts and strides, index tables with prefix sums) and upload it
+ * to the current CUDA device when one exists (other devices are uploaded on
+ * first use).  Required before any query or data movement.  Idempotent. */
+DTE_API int dte_type_commit(dte_type *type);
+
+/* Release a handle and set *type = NULL.  Device memory of the descriptor
+ * is kept until every operation enqueued with the type has completed
+ * (checked with CUDA events); for a type used inside CUDA graph capture it
+ * is kept until process exit.  Freeing a predefined handle is DTE_ERR_TYPE. */
+DTE_API int dte_type_free(dte_type *type);
+
+/* ------------------------------------------------------------------------
+ * Attributes (committed or not).
+ * ------------------------------------------------------------------------ */
+DTE_API int dte_type_size(dte_type type, int64_t *size);
+DTE_API int dte_type_get_extent(dte_type type, int64_t *lb, int64_t *extent);
+DTE_API int dte_type_get_true_extent(dte_type type, int64_t *true_lb, int64_t *true_extent);
+/* Number of merged segments of one element (the total of §3.1 iov_len). */
+DTE_API int dte_type_num_segments(dte_type type, int64_t *nseg);
+
+/* ------------------------------------------------------------------------
+ * Segment queries, §3.1.  A segment is a maximal run of typemap entries
+ * each starting exactly where the previous one ends, in typemap order.
+ * ------------------------------------------------------------------------ */
+
+/* MPIX_Type_iov_len: *iov_len = number of whole segments, counted from the
+ * first, whose bytes fit in max_iov_bytes; *actual_iov_bytes = their bytes.
+ * max_iov_bytes == -1 or >= size gives every segment.  Values below -1 are
+ * DTE_ERR_ARG.  Runs on the host over the committed descriptor, O(depth *
+ * log(entries)). */
+DTE_API int dte_type_iov_len(dte_type type, int64_t max_iov_bytes, int64_t *iov_len,
+                     int64_t *actual_iov_bytes);
+
+/* MPIX_Type_iov: segments [iov_offset, iov_offset + max_iov_len) of one
+ * element, written to the host array iov[]; iov_base is the segment's byte
+ * displacement from the buffer origin, cast to a pointer.  An offset at or
+ * past the end gives *actual_iov_len = 0.  Negative arguments: DTE_ERR_ARG. */
+DTE_API int dte_type_iov(dte_type type, int64_t iov_offset, dte_iov *iov, int64_t max_iov_len,
+                 int64_t *actual_iov_len);
+
+/* Device form of MPIX_Type_iov_len for a batch of n byte budgets: d_budget,
+ * d_iov_len and d_iov_bytes are device arrays of n int64.  A budget below -1
+ * yields -1 in both outputs.  Enqueued on `stream`. */
+DTE_API int dte_type_iov_len_async(dte_type type, int64_t n, const int64_t *d_budget,
+                           int64_t *d_iov_len, int64_t *d_iov_bytes, dte_stream_t stream);
+
+/* Device form of MPIX_Type_iov over `count` elements laid out at the extent
+ * (element e's segments shifted by e*extent, nothing merged across
+ * elements): writes segments [iov_offset, iov_offset + max_iov_len) to the
+ * device array d_iov with iov_base = base + displacement, and the number
+ * written to the device int64 *d_actual_iov_len (may be NULL).  `base` is
+ * only added, never dereferenced.  Enqueued on `stream`. */
+DTE_API int dte_type_iov_async(dte_type type, int64_t count, int64_t iov_offset, dte_iov *d_iov,
+                       int64_t max_iov_len, int64_t *d_actual_iov_len, const void *base,
+                       dte_stream_t stream);
+
+/* Device form of the byte-offset lookup the paper suggests doing with
+ * iov_len (§3.1, "bisect the byte offset of an arbitrary segment"): for each
+ * of n packed byte offsets d_offset[q] (0 <= offset < size of one element),
+ * write up to max_iov_len segments starting with the segment that contains
+ * that byte to d_iov[q * max_iov_len ...], the starting segment index to
+ * d_first[q] and the number written to d_actual[q].  Out-of-range offsets
+ * give d_first[q] = -1 and d_actual[q] = 0.  Enqueued on `stream`. */
+DTE_API int dte_type_iov_at_bytes_async(dte_type type, int64_t n, const int64_t *d_offset,
+                                int64_t max_iov_len, dte_iov *d_iov, int64_t *d_first,
+                                int64_t *d_actual, const void *base, dte_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Data movement (the datatype-engine half of §5.2's stream-enqueued
+ * send/recv of (buf, count, datatype)).
+ * ------------------------------------------------------------------------ */
+
+/* Bytes needed to pack incount elements: incount * size. */
+DTE_API int dte_pack_size(int64_t incount, dte_type type, int64_t *size);
+
+/* Gather incount elements of `type` (element e at inbuf + e*extent) into the
+ * contiguous outbuf at byte *position, then advance *position (on the host,
+ * at enqueue time).  inbuf/outbuf are device (or device-accessible pinned
+ * host) pointers; *position is a host int64.  DTE_ERR_TRUNCATE if
+ * outsize - *position < incount*size.  Bytes are copied verbatim (no value
+ * conversion).  Enqueued on `stream`; returns without waiting. */
+DTE_API int dte_pack_enqueue(const void *inbuf, int64_t incount, dte_type type, void *outbuf,
+                     int64_t outsize, int64_t *position, dte_stream_t stream);
+
+/* Scatter outcount elements from inbuf at byte *position into outbuf
+ * (element e at outbuf + e*extent), then advance *position.
+ * DTE_ERR_TRUNCATE if insize - *position < outcount*size; DTE_ERR_OVERLAP if
+ * two typemap bytes of the outcount elements coincide.  Enqueued on
+ * `stream`. */
+DTE_API int dte_unpack_enqueue(const void *inbuf, int64_t insize, int64_t *position, void *outbuf,
+                       int64_t outcount, dte_type type, dte_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DTE_H */

@@ -273,3 +273,36 @@ def subarray(sizes, subsizes, starts, old: OType, order: int = ORDER_C) -> OType
 
 def resized(old: OType, lb: int, extent: int) -> OType:
     return OType(lib().or_resized(old.h, lb, extent))
+
+
+_BASIC = {"byte": (1, 1), "int8": (1, 1), "uint8": (1, 1), "int16": (2, 2), "uint16": (2, 2),
+          "int32": (4, 4), "uint32": (4, 4), "int64": (8, 8), "uint64": (8, 8),
+          "float16": (2, 2), "bfloat16": (2, 2), "float32": (4, 4), "float64": (8, 8)}
+
+
+def from_spec(spec) -> OType:
+    """Build an oracle type from a nested spec tuple (see the package's inputs module)."""
+    k = spec[0]
+    if k == "basic":
+        return basic(*_BASIC[spec[1]])
+    if k == "contig":
+        return contiguous(spec[1], from_spec(spec[2]))
+    if k == "vector":
+        return vector(spec[1], spec[2], spec[3], from_spec(spec[4]))
+    if k == "hvector":
+        return hvector(spec[1], spec[2], spec[3], from_spec(spec[4]))
+    if k == "indexed":
+        return indexed(spec[1], spec[2], from_spec(spec[3]))
+    if k == "hindexed":
+        return hindexed(spec[1], spec[2], from_spec(spec[3]))
+    if k == "indexed_block":
+        return indexed_block(spec[1], spec[2], from_spec(spec[3]))
+    if k == "hindexed_block":
+        return hindexed_block(spec[1], spec[2], from_spec(spec[3]))
+    if k == "struct":
+        return struct(spec[1], spec[2], [from_spec(c) for c in spec[3]])
+    if k == "subarray":
+        return subarray(spec[1], spec[2], spec[3], from_spec(spec[5]), spec[4])
+    if k == "resized":
+        return resized(from_spec(spec[3]), spec[1], spec[2])
+    raise ValueError(f"unknown spec kind {k!r}")

@@ -11,6 +11,12 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")
     config.addinivalue_line("markers", "slow: long-running case")
+    # Build (or confirm up to date) the library and the oracle before any
+    # test module imports them.  Both builds are no-ops when nothing changed.
+    from paper_2402_12274_gb300 import build as _b
+    _b.build()
+    import oracle
+    oracle.build()
 
 
 def pytest_collection_modifyitems(config, items):

@@ -1,0 +1,21 @@
+"""Shared test helpers: build the same spec on both sides and compare."""
+import numpy as np
+
+import oracle
+import paper_2402_12274_gb300 as dte
+
+
+def both(spec, commit=True):
+    t = dte.Datatype.from_spec(spec)
+    if t.h in {b.h for b in dte._BASIC_BY_NAME.values()}:
+        t = dte.Datatype.contiguous(1, t)
+    if commit:
+        t.commit()
+    return t, oracle.from_spec(spec)
+
+
+def iov_arrays(t, offset=0, max_len=None):
+    lst = t.iov(offset, max_len)
+    d = np.array([a for a, _ in lst], np.int64)
+    l = np.array([b for _, b in lst], np.int64)
+    return d, l

@@ -1,0 +1,328 @@
+"""GPU parity: pack / unpack / segment enumeration through the C ABI on the
+device, compared byte for byte (and index for index) with the CPU oracle on
+the same seeded inputs.  Source bytes are raw random bytes, so NaN payloads
+and every bit pattern must survive verbatim."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2402_12274_gb300 import inputs
+from tests.helpers import both
+
+torch = pytest.importorskip("torch")
+import paper_2402_12274_gb300 as dte  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+SENT = 0xA5
+
+
+def span_of(o, count):
+    """(lo, hi) byte range touched by `count` elements, relative to displacement 0."""
+    if o.size == 0 or count == 0:
+        return 0, 0
+    ends = [e * o.extent for e in (0, count - 1)]
+    lo = min(e + o.true_lb for e in ends)
+    hi = max(e + o.true_lb + o.true_extent for e in ends)
+    return lo, hi
+
+
+def gpu_pack(t, src_np, count, base, pk_pos=0, stream=None):
+    s = stream or torch.cuda.current_stream()
+    d_src = torch.from_numpy(src_np).to(DEV)
+    out = torch.full((pk_pos + count * t.size + 16,), SENT, dtype=torch.uint8, device=DEV)
+    pos = dte.pack(d_src, count, t, out, pk_pos, s, src_offset=base)
+    s.synchronize()
+    assert pos == pk_pos + count * t.size
+    o = out.cpu().numpy()
+    assert np.all(o[:pk_pos] == SENT) and np.all(o[pos:] == SENT), "pack wrote outside its range"
+    return o[pk_pos:pos]
+
+
+def gpu_unpack(t, packed_np, count, span, base, pk_pos=0):
+    s = torch.cuda.current_stream()
+    buf = np.full(pk_pos + packed_np.size, SENT, np.uint8)
+    buf[pk_pos:] = packed_np
+    d_pk = torch.from_numpy(buf).to(DEV)
+    d_dst = torch.full((span,), SENT, dtype=torch.uint8, device=DEV)
+    pos = dte.unpack(d_pk, pk_pos, d_dst, count, t, s, dst_offset=base)
+    s.synchronize()
+    assert pos == pk_pos + count * t.size
+    return d_dst.cpu().numpy()
+
+
+def check_move(spec, count, rng, misalign=True):
+    t, o = both(spec)
+    if o.size == 0:
+        return
+    lo, hi = span_of(o, count)
+    shift = int(rng.integers(0, 16)) if misalign else 0
+    base = -lo + shift
+    span = hi - lo + shift + 1
+    src = rng.integers(0, 256, span, dtype=np.uint8)
+    ref = o.pack(src, count, base)
+    pk_pos = int(rng.integers(0, 20)) if misalign else 0
+    got = gpu_pack(t, src, count, base, pk_pos)
+    assert np.array_equal(got, ref), spec
+    if o.overlaps(count):
+        with pytest.raises(dte.DteError) as e:
+            gpu_unpack(t, ref, count, span, base, pk_pos)
+        assert e.value.code == dte.ERR_OVERLAP
+        return
+    want = np.full(span, SENT, np.uint8)
+    o.unpack(ref, count, want, base)
+    got = gpu_unpack(t, ref, count, span, base, pk_pos)
+    assert np.array_equal(got, want), spec
+
+
+def test_random_nests_pack_unpack():
+    rng = np.random.default_rng(201)
+    for i in range(600):
+        check_move(inputs.random_spec(rng, big=i % 3 == 0), int(rng.integers(1, 4)), rng)
+
+
+def test_merging_layouts_pack_unpack():
+    rng = np.random.default_rng(202)
+    for _ in range(200):
+        check_move(inputs.sequential_spec(rng), int(rng.integers(1, 4)), rng)
+
+
+def test_aligned_word_sizes():
+    # runs whose lengths and offsets allow 16/8/4/2/1-byte words
+    rng = np.random.default_rng(203)
+    for el, bl, st in [("float64", 2, 6), ("float64", 1, 3), ("float32", 1, 3), ("float32", 4, 16),
+                       ("bfloat16", 3, 7), ("byte", 5, 9), ("int16", 8, 8)]:
+        for count in (1, 2, 7):
+            for mis in (False, True):
+                check_move(("vector", 37, bl, st, ("basic", el)), count, rng, misalign=mis)
+
+
+def iov_check(t, o, count, first, n):
+    d_iov = torch.zeros((max(n, 1), 2), dtype=torch.int64, device=DEV)
+    d_act = torch.full((1,), -7, dtype=torch.int64, device=DEV)
+    base = 1 << 40
+    dte.dte_type_iov_async(t.h, count, first, d_iov.data_ptr(), n, d_act.data_ptr(), base,
+                           torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    od, ol = o.iov_elements(count, first, n)
+    got = d_iov.cpu().numpy()[: len(od)]
+    assert int(d_act.item()) == len(od)
+    assert np.array_equal(got[:, 0] - base, od) and np.array_equal(got[:, 1], ol)
+
+
+def test_random_nests_iov_device():
+    rng = np.random.default_rng(204)
+    for i in range(300):
+        spec = inputs.random_spec(rng) if i % 2 else inputs.sequential_spec(rng)
+        t, o = both(spec)
+        count = int(rng.integers(1, 4))
+        total = count * o.iov_count()
+        for first in (0, total // 2):
+            iov_check(t, o, count, first, total + 3)
+
+
+def test_iov_len_and_at_bytes_device():
+    rng = np.random.default_rng(205)
+    s = torch.cuda.current_stream().cuda_stream
+    for i in range(200):
+        spec = inputs.random_spec(rng, big=True) if i % 2 else inputs.sequential_spec(rng)
+        t, o = both(spec)
+        if o.size == 0:
+            continue
+        budgets = np.unique(np.concatenate([rng.integers(-3, o.size + 4, 64), [-1, 0, o.size]])).astype(np.int64)
+        d_b = torch.from_numpy(budgets).to(DEV)
+        d_n = torch.empty_like(d_b)
+        d_y = torch.empty_like(d_b)
+        dte.dte_type_iov_len_async(t.h, budgets.size, d_b.data_ptr(), d_n.data_ptr(), d_y.data_ptr(), s)
+        torch.cuda.synchronize()
+        for b, n, y in zip(budgets, d_n.cpu().numpy(), d_y.cpu().numpy()):
+            if b < -1:
+                assert (n, y) == (-1, -1)
+            else:
+                assert (n, y) == o.iov_len(int(b)), (spec, b)
+        # byte offset -> the segment containing it, and the next segments
+        offs = rng.integers(-2, o.size + 2, 40).astype(np.int64)
+        m = 3
+        d_o = torch.from_numpy(offs).to(DEV)
+        d_iov = torch.zeros((offs.size * m, 2), dtype=torch.int64, device=DEV)
+        d_f = torch.empty_like(d_o)
+        d_a = torch.empty_like(d_o)
+        dte.dte_type_iov_at_bytes_async(t.h, offs.size, d_o.data_ptr(), m, d_iov.data_ptr(), d_f.data_ptr(),
+                                        d_a.data_ptr(), 0, s)
+        torch.cuda.synchronize()
+        f, a, iv = d_f.cpu().numpy(), d_a.cpu().numpy(), d_iov.cpu().numpy()
+        sd, sl = o.iov()
+        for q, b in enumerate(offs):
+            if b < 0 or b >= o.size:
+                assert (f[q], a[q]) == (-1, 0)
+                continue
+            k = o.iov_len(int(b))[0]
+            assert f[q] == k and a[q] == min(m, len(sd) - k)
+            got = iv[q * m: q * m + a[q]]
+            assert np.array_equal(got[:, 0], sd[k:k + a[q]]) and np.array_equal(got[:, 1], sl[k:k + a[q]])
+
+
+# --------------------------------------------------------------------------
+# workload layouts
+# --------------------------------------------------------------------------
+def test_strided_vector_workload():
+    # vector(1024, 4, 16) of float32, 64 elements, values U[-1,1) seed 1
+    spec = inputs.strided_vector_spec()
+    t, o = both(spec)
+    count = 64
+    lo, hi = span_of(o, count)
+    src = inputs.uniform_f32(hi // 4, 1).view(np.uint8)
+    ref = o.pack(src, count)
+    assert ref.size == 1 << 20
+    got = gpu_pack(t, src, count, 0)
+    assert np.array_equal(got, ref)
+    want = np.full(hi, SENT, np.uint8)
+    o.unpack(ref, count, want)
+    assert np.array_equal(gpu_unpack(t, ref, count, hi, 0), want)
+    iov_check(t, o, count, 0, count * 1024)
+    d = torch.empty((count * 1024, 2), dtype=torch.int64, device=DEV)
+    dte.dte_type_iov_async(t.h, count, 0, d.data_ptr(), count * 1024, 0, 0, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert np.all(d[:, 1].cpu().numpy() == 16)
+
+
+@pytest.mark.parametrize("n", [16, 64])
+def test_halo_faces_small(n):
+    check_halo(n)
+
+
+def check_halo(n, g=2):
+    send = inputs.all_faces_struct(inputs.halo_face_specs(n, g))
+    recv = inputs.all_faces_struct(inputs.halo_recv_face_specs(n, g))
+    ts, os_ = both(send)
+    tr, or_ = both(recv)
+    grid = inputs.normal_f64(n ** 3, 2).view(np.uint8)
+    ref = os_.pack(grid, 1)
+    d_grid = torch.from_numpy(grid).to(DEV)
+    d_pk = torch.empty(ts.size, dtype=torch.uint8, device=DEV)
+    s = torch.cuda.current_stream()
+    dte.pack(d_grid, 1, ts, d_pk, 0, s)
+    d_g2 = torch.full((grid.size,), SENT, dtype=torch.uint8, device=DEV)
+    dte.unpack(d_pk, 0, d_g2, 1, tr, s)
+    s.synchronize()
+    assert np.array_equal(d_pk.cpu().numpy(), ref)
+    want = np.full(grid.size, SENT, np.uint8)
+    or_.unpack(ref, 1, want)
+    assert np.array_equal(d_g2.cpu().numpy(), want)
+
+
+@pytest.mark.slow
+def test_halo_faces_full_size():
+    check_halo(512)
+
+
+@pytest.mark.parametrize("nblocks", [1 << 12, 1 << 16])
+def test_record_indexed_workload(nblocks):
+    check_record_indexed(nblocks)
+
+
+@pytest.mark.slow
+def test_record_indexed_full_size():
+    check_record_indexed(1 << 22)
+
+
+def check_record_indexed(nblocks):
+    rng = np.random.default_rng(3)
+    spec = inputs.record_indexed_spec(rng, nblocks)
+    t, o = both(spec)
+    span = o.true_lb + o.true_extent
+    src = inputs.random_bytes(span, 3)
+    ref = o.pack(src, 1)
+    got = gpu_pack(t, src, 1, 0)
+    assert np.array_equal(got, ref)
+    want = np.full(span, SENT, np.uint8)
+    o.unpack(ref, 1, want)
+    assert np.array_equal(gpu_unpack(t, ref, 1, span, 0), want)
+    # iov queried in chunks of 4096 from random packed byte offsets
+    offs = np.sort(rng.integers(0, o.size, 64)).astype(np.int64)
+    m = 4096
+    d_o = torch.from_numpy(offs).to(DEV)
+    d_iov = torch.zeros((offs.size * m, 2), dtype=torch.int64, device=DEV)
+    d_f = torch.empty_like(d_o)
+    d_a = torch.empty_like(d_o)
+    dte.dte_type_iov_at_bytes_async(t.h, offs.size, d_o.data_ptr(), m, d_iov.data_ptr(), d_f.data_ptr(),
+                                    d_a.data_ptr(), 0, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    f, a, iv = d_f.cpu().numpy(), d_a.cpu().numpy(), d_iov.cpu().numpy()
+    for q, b in enumerate(offs):
+        e, r = divmod(int(b), 52)          # closed form of the record layout
+        k = 2 * e + (r >= 12)
+        assert f[q] == k
+        od, ol = o.iov(k, m)
+        assert a[q] == len(od)
+        got = iv[q * m: q * m + a[q]]
+        assert np.array_equal(got[:, 0], od) and np.array_equal(got[:, 1], ol)
+
+
+# --------------------------------------------------------------------------
+# stream semantics, lifetime and errors
+# --------------------------------------------------------------------------
+def test_stream_ordered_pipeline_without_host_sync():
+    # produce -> pack -> unpack -> consume on one non-default stream
+    spec = ("vector", 4096, 3, 7, ("basic", "float32"))
+    t, o = both(spec)
+    s = torch.cuda.Stream()
+    n = 4096 * 7
+    with torch.cuda.stream(s):
+        x = torch.arange(n, dtype=torch.float32, device=DEV) * 0.5 - 3.0
+        pk = torch.empty(t.size, dtype=torch.uint8, device=DEV)
+        dte.pack(x, 1, t, pk, 0, s)
+        y = torch.zeros(n, dtype=torch.float32, device=DEV)
+        dte.unpack(pk, 0, y, 1, t, s)
+        z = y * 2.0 + 1.0
+    s.synchronize()
+    xr = (np.arange(n, dtype=np.float32) * 0.5 - 3.0)
+    yr = np.zeros(n, np.float32).view(np.uint8)
+    o.unpack(o.pack(xr.view(np.uint8), 1), 1, yr)
+    assert np.array_equal(z.cpu().numpy(), yr.view(np.float32) * 2.0 + 1.0)
+
+
+def test_free_while_enqueued_keeps_descriptor():
+    rng = np.random.default_rng(206)
+    spec = inputs.record_indexed_spec(rng, 1 << 15)
+    t, o = both(spec)
+    span = o.true_lb + o.true_extent
+    src = inputs.random_bytes(span, 4)
+    d_src = torch.from_numpy(src).to(DEV)
+    s = torch.cuda.Stream()
+    outs = []
+    with torch.cuda.stream(s):
+        torch.cuda._sleep(2_000_000)  # keep the stream busy so the packs are still queued
+        for _ in range(3):
+            pk = torch.empty(t.size, dtype=torch.uint8, device=DEV)
+            dte.pack(d_src, 1, t, pk, 0, s)
+            outs.append(pk)
+    del t  # free the handle while its kernels are queued
+    s.synchronize()
+    ref = o.pack(src, 1)
+    for pk in outs:
+        assert np.array_equal(pk.cpu().numpy(), ref)
+
+
+def test_enqueue_errors():
+    t = dte.Datatype.vector(4, 1, 2, dte.FLOAT32)
+    buf = torch.zeros(64, dtype=torch.uint8, device=DEV)
+    with pytest.raises(dte.DteError) as e:
+        dte.pack(buf, 1, t, buf, 0)
+    assert e.value.code == dte.ERR_TYPE  # not committed
+    t.commit()
+    small = torch.zeros(15, dtype=torch.uint8, device=DEV)
+    with pytest.raises(dte.DteError) as e:
+        dte.pack(buf, 1, t, small, 0)
+    assert e.value.code == dte.ERR_TRUNCATE
+    with pytest.raises(dte.DteError) as e:
+        dte.pack(buf, 1, t, buf, 60)
+    assert e.value.code == dte.ERR_TRUNCATE
+    ov = dte.Datatype.vector(4, 3, 2, dte.FLOAT32).commit()
+    with pytest.raises(dte.DteError) as e:
+        dte.unpack(buf, 0, buf, 1, ov)
+    assert e.value.code == dte.ERR_OVERLAP
+    assert dte.pack(buf, 0, t, small, 0) == 0  # empty op: nothing enqueued
+    with pytest.raises(dte.DteError) as e:
+        dte.dte_pack_enqueue(0, 1, t.h, buf.data_ptr(), 64, 0, 0)
+    assert e.value.code == dte.ERR_ARG
