@@ -13,8 +13,8 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "slow: long-running case")
     # Build (or confirm up to date) the library and the oracle before any
     # test module imports them.  Both builds are no-ops when nothing changed.
-    from paper_2402_12274_gb300 import build as _b
-    _b.build()
+    import __graft_entry__
+    __graft_entry__._load_builder().build()
     import oracle
     oracle.build()
 
