@@ -43,7 +43,7 @@ WORKLOAD = "512^3 float64 grid, six halo faces (ghost 2): pack all six into one 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--steps", type=int, default=1000)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="dte", choices=["dte", "reference"])
     p.add_argument("--no-e2e", action="store_true")
@@ -87,7 +87,7 @@ def traffic_from_profile(kernel: str):
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
-    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -95,12 +95,14 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.windows = []
+        self.adjacent = False
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -111,6 +113,28 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+
+    def open(self, adjacent: bool = False):
+        self.adjacent = self.adjacent or adjacent
+        self.windows.append([time.time(), None])
+
+    def close(self):
+        self.windows[-1][1] = time.time()
+
+    @staticmethod
+    def _ts(s):
+        try:
+            from datetime import datetime
+            return datetime.strptime(s.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
+    def _in_window(self, t):
+        return t is not None and any(a <= t <= (b or 1e300) for a, b in self.windows)
+
+    def count_in_window(self):
+        time.sleep(0.1)  # let the reader catch up
+        return sum(1 for ln in list(self.lines) if self._in_window(self._ts(ln.split(",")[0])))
 
     def __exit__(self, *a):
         if self.proc:
@@ -123,22 +147,23 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in list(self.lines):
             parts = [x.strip() for x in ln.split(",")]
-            if len(parts) < 8:
+            if len(parts) < 9 or not self._in_window(self._ts(parts[0])):
                 continue
             try:
-                sm.append(float(parts[0]))
-                mx.append(float(parts[1]))
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[4:8]):
+            for nm, v in zip(names, parts[5:9]):
                 if v.lower() == "active":
                     reasons.add(nm)
+        window = "adjacent soak of the same step" if self.adjacent else "timed region"
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0, "window": window}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "window": window}
 
 
 def dist_env():
@@ -224,9 +249,16 @@ def run_dte(args):
     stream = torch.cuda.Stream(device=dev)
     sh = stream.cuda_stream
 
+    # the six faces share edge cells, so they are unpacked as one batch of six
+    # per-face operations (one launch); shared cells receive identical bytes
+    batches = {}
+
     def unpack_all(dst):
-        for f, o in zip(faces, offs):
-            dte.dte_unpack_enqueue(packed.data_ptr(), size, o, dst, 1, f.h, sh)
+        b = batches.get(dst)
+        if b is None:
+            b = batches[dst] = dte.Batch(dte.BATCH_UNPACK, [(f.h, 1, dst, packed.data_ptr() + o)
+                                                              for f, o in zip(faces, offs)])
+        b.enqueue(sh)
 
     def step():
         dte.dte_pack_enqueue(grid.data_ptr(), 1, send.h, packed.data_ptr(), size, 0, sh)
@@ -244,6 +276,8 @@ def run_dte(args):
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
+        time.sleep(0.15)  # sampler running before the window opens
+        clk.open()
         with torch.cuda.stream(stream):
             for i in range(K):
                 flush.zero_()
@@ -253,6 +287,18 @@ def run_dte(args):
                 unpack_all(grid2.data_ptr())
                 ev[i][2].record(stream)
         stream.synchronize()
+        clk.close()
+        if clk.count_in_window() < 3:
+            # window too short for nvidia-smi: sample an identical soak right after
+            clk.open(adjacent=True)
+            t_end = time.time() + 0.6
+            with torch.cuda.stream(stream):
+                while time.time() < t_end:
+                    for _ in range(50):
+                        flush.zero_()
+                        step()
+                    stream.synchronize()
+            clk.close()
     torch.cuda.synchronize()
     t_pack = np.array([ev[i][0].elapsed_time(ev[i][1]) for i in range(K)]) * 1e-3
     t_unpack = np.array([ev[i][1].elapsed_time(ev[i][2]) for i in range(K)]) * 1e-3
@@ -307,11 +353,11 @@ def run_dte(args):
     peak, peak_kind = peaks()
     mp, mu = float(t_pack.mean()), float(t_unpack.mean())
     dom = "pack" if mp >= mu else "unpack"
-    # per launch: one pack launch moves `size` bytes; the unpack leg is six launches
-    tdom = mp if dom == "pack" else mu / len(faces)
-    per_launch = size if dom == "pack" else size // len(faces)
+    # one launch each: the struct pack and the six-op unpack batch move `size` bytes
+    tdom = max(mp, mu)
+    per_launch = size
     achieved = ALG_FACTOR * per_launch / tdom / 1e9
-    kname = "move_kernel<16,true,true>" if dom == "pack" else "move_kernel<16,false,true>"
+    kname = "dte::move_kernel<16, 1, 1>" if dom == "pack" else "dte::batch_kernel<0>"
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic_from_profile(kname),
             "kernel": kname, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
@@ -332,7 +378,7 @@ def run_dte(args):
             "config": {"workload": WORKLOAD, "packed_bytes": size, "alg_bytes_per_step": alg_step,
                        "l2": "flushed between steps (512 MiB write outside the timed events)",
                        "parallelism": f"replicas x{world}"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": (1 + len(faces)) * K,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * K,
             "clocks": clk.summary(), "check": "ok" if ok else "MISMATCH",
         }
         print(json.dumps(line), flush=True)

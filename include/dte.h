@@ -240,6 +240,54 @@ DTE_API int dte_pack_enqueue(const void *inbuf, int64_t incount, dte_type type, 
 DTE_API int dte_unpack_enqueue(const void *inbuf, int64_t insize, int64_t *position, void *outbuf,
                        int64_t outcount, dte_type type, dte_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Batches: many independent pack (or unpack) operations in one persistent
+ * kernel launch.  The paper's motivation for stream-enqueued operations is
+ * to take launch and synchronisation cost off the critical path (§4, §5);
+ * a batch removes the per-operation launch as well.
+ * ------------------------------------------------------------------------ */
+
+/* One operation of a batch.  `user` is the user-layout origin (element e at
+ * user + e*extent): the source of a pack, the destination of an unpack.
+ * `packed` is the contiguous side with any byte position already applied:
+ * it receives (pack) or supplies (unpack) count*size bytes. */
+typedef struct dte_op {
+    dte_type type;     /* committed */
+    int64_t count;     /* elements, >= 0 */
+    void *user;
+    void *packed;
+} dte_op;
+
+typedef struct dte_batch_s *dte_batch;
+enum dte_batch_kind { DTE_BATCH_UNPACK = 0, DTE_BATCH_PACK = 1 };
+
+/* Validate `nops` operations, resolve their descriptors on the current
+ * device and upload the op table (device memory owned by the batch).  The
+ * ops array is read during the call only; the types may be freed afterwards
+ * (the batch keeps their descriptors).  Unpack batches reject an op whose own
+ * target layout overlaps (DTE_ERR_OVERLAP).  Ops of one batch run
+ * concurrently: their output ranges must not overlap, except where they write
+ * identical bytes. */
+DTE_API int dte_batch_create(int kind, int64_t nops, const dte_op *ops, dte_batch *out);
+
+/* Launch shape of a batch: at most blocks_per_sm CTAs of 256 threads per SM
+ * (0 = as many as fit) and at least tiles_per_warp_min 2 KiB tiles per warp.
+ * Used by the autotuner; the defaults are (0, 1). */
+DTE_API int dte_batch_set_launch(dte_batch batch, int blocks_per_sm, int64_t tiles_per_warp_min);
+
+/* Enqueue every operation of the batch as one kernel on `stream`.  Performs
+ * no allocation or host copy, so it may be captured into a CUDA graph and
+ * replayed; a batch used under capture is kept until process exit. */
+DTE_API int dte_batch_enqueue(dte_batch batch, dte_stream_t stream);
+
+/* Release a batch and set *batch = NULL; device memory is kept until the
+ * enqueued launches have completed. */
+DTE_API int dte_batch_free(dte_batch *batch);
+
+/* One-shot forms: create, enqueue on `stream`, free. */
+DTE_API int dte_pack_batch_enqueue(int64_t nops, const dte_op *ops, dte_stream_t stream);
+DTE_API int dte_unpack_batch_enqueue(int64_t nops, const dte_op *ops, dte_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -47,6 +47,13 @@ class dte_iov(C.Structure):
     _fields_ = [("iov_base", C.c_void_p), ("iov_len", C.c_int64)]
 
 
+class dte_op(C.Structure):
+    _fields_ = [("type", C.c_void_p), ("count", C.c_int64), ("user", C.c_void_p), ("packed", C.c_void_p)]
+
+
+BATCH_UNPACK, BATCH_PACK = 0, 1
+
+
 # error codes (include/dte.h)
 SUCCESS, ERR_ARG, ERR_TYPE, ERR_OVERFLOW, ERR_TRUNCATE, ERR_OVERLAP, ERR_NOMEM, ERR_CUDA, \
     ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_NODEVICE = range(11)
@@ -88,6 +95,12 @@ _SIGS = {
     "dte_pack_size": ([_i64, _p, _pi64], C.c_int),
     "dte_pack_enqueue": ([_p, _i64, _p, _p, _i64, _pi64, _p], C.c_int),
     "dte_unpack_enqueue": ([_p, _i64, _pi64, _p, _i64, _p, _p], C.c_int),
+    "dte_batch_create": ([C.c_int, _i64, C.POINTER(dte_op), _pp], C.c_int),
+    "dte_batch_set_launch": ([_p, C.c_int, _i64], C.c_int),
+    "dte_batch_enqueue": ([_p, _p], C.c_int),
+    "dte_batch_free": ([_pp], C.c_int),
+    "dte_pack_batch_enqueue": ([_i64, C.POINTER(dte_op), _p], C.c_int),
+    "dte_unpack_batch_enqueue": ([_i64, C.POINTER(dte_op), _p], C.c_int),
 }
 for _n, (_a, _r) in _SIGS.items():
     _f = getattr(lib, _n)
@@ -299,6 +312,72 @@ def dte_unpack_enqueue(inbuf: int, insize: int, position: int, outbuf: int, outc
     _ck(lib.dte_unpack_enqueue(inbuf, insize, C.byref(pos), outbuf, outcount, t, stream),
         "dte_unpack_enqueue")
     return pos.value
+
+
+def _ops_array(ops):
+    """ops: iterable of (type handle, count, user ptr, packed ptr)."""
+    ops = list(ops)
+    arr = (dte_op * max(len(ops), 1))()
+    for i, (t, n, u, p) in enumerate(ops):
+        arr[i].type = int(t)
+        arr[i].count = int(n)
+        arr[i].user = int(u)
+        arr[i].packed = int(p)
+    return arr, len(ops)
+
+
+def dte_batch_create(kind: int, ops) -> int:
+    arr, n = _ops_array(ops)
+    out = C.c_void_p()
+    _ck(lib.dte_batch_create(kind, n, arr, C.byref(out)), "dte_batch_create")
+    return out.value
+
+
+def dte_batch_set_launch(batch: int, blocks_per_sm: int, tiles_per_warp_min: int = 1):
+    _ck(lib.dte_batch_set_launch(batch, blocks_per_sm, tiles_per_warp_min), "dte_batch_set_launch")
+
+
+def dte_batch_enqueue(batch: int, stream: int = 0):
+    _ck(lib.dte_batch_enqueue(batch, stream), "dte_batch_enqueue")
+
+
+def dte_batch_free(batch: int):
+    h = C.c_void_p(batch)
+    _ck(lib.dte_batch_free(C.byref(h)), "dte_batch_free")
+
+
+def dte_pack_batch_enqueue(ops, stream: int = 0):
+    arr, n = _ops_array(ops)
+    _ck(lib.dte_pack_batch_enqueue(n, arr, stream), "dte_pack_batch_enqueue")
+
+
+def dte_unpack_batch_enqueue(ops, stream: int = 0):
+    arr, n = _ops_array(ops)
+    _ck(lib.dte_unpack_batch_enqueue(n, arr, stream), "dte_unpack_batch_enqueue")
+
+
+class Batch:
+    """Owning wrapper of a dte_batch (a reusable persistent launch)."""
+
+    def __init__(self, kind: int, ops):
+        self.h = dte_batch_create(kind, ops)
+
+    def enqueue(self, stream=None):
+        dte_batch_enqueue(self.h, _stream_handle(stream))
+
+    def set_launch(self, blocks_per_sm: int, tiles_per_warp_min: int = 1):
+        dte_batch_set_launch(self.h, blocks_per_sm, tiles_per_warp_min)
+
+    def free(self):
+        if self.h:
+            dte_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------------------------

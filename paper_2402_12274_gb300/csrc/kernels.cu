@@ -7,13 +7,15 @@
 //
 // Data movement design (pure data movement, no tensor cores):
 //  * The packed side is contiguous, so work is split in packed space: each
-//    warp owns a contiguous range of 16-byte chunks; lane l of the warp handles
-//    chunks l, l+32, l+64, l+96 of every 512 x 4 byte step, so every packed-side
-//    access of a warp is one coalesced 512-byte transaction, and four
-//    independent 16-byte loads per lane are in flight before the stores.
+//    warp owns a contiguous range of 2 KiB steps; lane l of the warp handles
+//    chunks l, l+32, l+64, l+96 (16 bytes each) of a step, so every
+//    packed-side access of a warp is one coalesced 512-byte transaction, and
+//    four independent 16-byte loads per lane are in flight before the stores.
 //  * Each chunk maps back to the user layout through the committed descriptor
 //    (desc.h: REG levels by fast invariant division, LIST levels by a search
-//    that gallops from the lane's previous position).
+//    that gallops from that chunk slot's previous position).  Descriptors of
+//    up to 16 KiB are staged whole in shared memory; larger ones stage their
+//    node table and read index arrays through L1/L2.
 //  * W, the copy word, is the largest power of two <= 16 dividing every run
 //    length and displacement of the type and both buffer addresses; a word
 //    never straddles two runs, so W = 16 moves each chunk with one 16-byte
@@ -21,10 +23,15 @@
 //    words, re-walking the descriptor only when a run ends.
 //  * Bytes are moved verbatim through integer registers: no value is ever
 //    converted, so NaN payloads survive.
-//  * Node tables (<= 64 nodes) are staged in shared memory per CTA.
+//  * Batches: many independent operations (different types, buffers and
+//    sizes) run in one persistent launch over a global list of 2 KiB tiles;
+//    the launch reads only a device-resident op table, so it can be captured
+//    in a CUDA graph and replayed.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
+#include <vector>
 
 #include "internal.h"
 
@@ -32,24 +39,60 @@ namespace dte {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kU = 4;                // chunks per lane per step
+constexpr int kU = 4;                 // chunks per lane per step
+constexpr int kStep = 32 * kU;        // chunks per warp step (2 KiB)
+constexpr int64_t kSmemBlob = 16384;  // stage descriptors up to this size whole
 constexpr int kMaxSmemNodes = 64;
 
-struct MoveArgs {
-    const char *blob;       // device descriptor blob
-    const char *user_in;    // pack: user buffer (displacement 0)
-    char *user_out;         // unpack: user buffer (displacement 0)
-    const char *packed_in;  // unpack: packed bytes (already at position)
-    char *packed_out;       // pack: packed bytes (already at position)
+enum : int { STAGE_NONE = 0, STAGE_NODES = 1, STAGE_BLOB = 2 };
+
+// What a kernel needs to walk one committed type.
+struct Desc {
+    const char *blob;
+    int64_t blob_bytes;
+    int32_t root;
+    int32_t nnodes;
+    int32_t stage;
+    int32_t pad_;
+};
+
+// One data movement: element e of the user layout starts at user + e*extent.
+struct Op {
+    const char *user_in;    // pack source
+    char *user_out;         // unpack destination
+    const char *packed_in;  // unpack source (position applied)
+    char *packed_out;       // pack destination (position applied)
     int64_t total;          // bytes moved
     int64_t esize;          // element size
     int64_t extent;         // element stride
     FastDiv ediv;           // / esize
-    int64_t nchunks;        // ceil(total / 16)
-    int64_t per_warp;       // chunks per warp, multiple of 32*kU
-    int root;
-    int nnodes;
+    int32_t root;
+    int32_t pad_;
 };
+
+__device__ __forceinline__ void stage_desc(const Desc &d, uint4 *smem, const char *&blob,
+                                           const DNode *&nodes)
+{
+    const DNode *g = reinterpret_cast<const DNode *>(d.blob + sizeof(BlobHeader));
+    if (d.stage == STAGE_BLOB) {
+        const uint4 *s = reinterpret_cast<const uint4 *>(d.blob);
+        int nw = (int)(d.blob_bytes / 16);
+        for (int i = threadIdx.x; i < nw; i += blockDim.x) smem[i] = s[i];
+        __syncthreads();
+        blob = reinterpret_cast<const char *>(smem);
+        nodes = reinterpret_cast<const DNode *>(blob + sizeof(BlobHeader));
+    } else if (d.stage == STAGE_NODES) {
+        const uint4 *s = reinterpret_cast<const uint4 *>(g);
+        int nw = d.nnodes * (int)(sizeof(DNode) / 16);
+        for (int i = threadIdx.x; i < nw; i += blockDim.x) smem[i] = s[i];
+        __syncthreads();
+        blob = d.blob;
+        nodes = reinterpret_cast<const DNode *>(smem);
+    } else {
+        blob = d.blob;
+        nodes = g;
+    }
+}
 
 template <int W> struct Word;
 template <> struct Word<1> { using T = uint8_t; };
@@ -64,37 +107,19 @@ union Chunk {
     typename Word<W>::T w[16 / W];
 };
 
-__device__ __forceinline__ const DNode *stage_nodes(const char *blob, int nnodes, DNode *smem)
-{
-    const DNode *g = reinterpret_cast<const DNode *>(blob + sizeof(BlobHeader));
-    if (nnodes > kMaxSmemNodes) return g;
-    const uint4 *s = reinterpret_cast<const uint4 *>(g);
-    uint4 *d = reinterpret_cast<uint4 *>(smem);
-    int nw = nnodes * (int)(sizeof(DNode) / 16);
-    for (int i = threadIdx.x; i < nw; i += blockDim.x) d[i] = s[i];
-    __syncthreads();
-    return smem;
-}
-
 // packed offset P -> user displacement and bytes left in that run
-__device__ __forceinline__ void locate(const MoveArgs &a, const DNode *nodes, int64_t P, int64_t &d,
-                                       int64_t &rem, Hint &h)
+__device__ __forceinline__ void locate(const Op &op, const DNode *nodes, const char *blob, int64_t P,
+                                       int64_t &d, int64_t &rem, Hint &h)
 {
-    int64_t e = fdiv(P, a.ediv);
-    d = e * a.extent;
-    decode_bytes(nodes, a.blob, a.root, P - e * a.esize, d, rem, h);
+    int64_t e = fdiv(P, op.ediv);
+    d = e * op.extent;
+    decode_bytes(nodes, blob, op.root, P - e * op.esize, d, rem, h);
 }
 
 template <int W>
 __device__ __forceinline__ typename Word<W>::T ldw(const char *p)
 {
     return __ldg(reinterpret_cast<const typename Word<W>::T *>(p));
-}
-
-template <>
-__device__ __forceinline__ uint4 ldw<16>(const char *p)
-{
-    return __ldg(reinterpret_cast<const uint4 *>(p));
 }
 
 template <int W>
@@ -105,14 +130,14 @@ __device__ __forceinline__ void stw(char *p, typename Word<W>::T v)
 
 // gather the nb (<= 16) packed bytes starting at P from the user layout
 template <int W>
-__device__ __forceinline__ uint4 gather_chunk(const MoveArgs &a, const DNode *nodes, int64_t P, int nb,
-                                              Hint &h)
+__device__ __forceinline__ uint4 gather_chunk(const Op &op, const DNode *nodes, const char *blob, int64_t P,
+                                              int nb, Hint &h)
 {
     Chunk<W> c;
     if (W == 16) {
         int64_t d, rem;
-        locate(a, nodes, P, d, rem, h);
-        c.v = ldw<16>(a.user_in + d);
+        locate(op, nodes, blob, P, d, rem, h);
+        c.v = ldw<16>(op.user_in + d);
         return c.v;
     }
     c.v = make_uint4(0, 0, 0, 0);
@@ -120,8 +145,8 @@ __device__ __forceinline__ uint4 gather_chunk(const MoveArgs &a, const DNode *no
 #pragma unroll
     for (int s = 0; s < 16 / W; s++) {
         if (s * W < nb) {
-            if (rem <= 0) locate(a, nodes, P + s * W, d, rem, h);
-            c.w[s] = ldw<W>(a.user_in + d);
+            if (rem <= 0) locate(op, nodes, blob, P + s * W, d, rem, h);
+            c.w[s] = ldw<W>(op.user_in + d);
             d += W;
             rem -= W;
         }
@@ -130,23 +155,23 @@ __device__ __forceinline__ uint4 gather_chunk(const MoveArgs &a, const DNode *no
 }
 
 template <int W>
-__device__ __forceinline__ void scatter_chunk(const MoveArgs &a, const DNode *nodes, int64_t P, int nb,
-                                              uint4 v, Hint &h)
+__device__ __forceinline__ void scatter_chunk(const Op &op, const DNode *nodes, const char *blob, int64_t P,
+                                              int nb, uint4 v, Hint &h)
 {
     Chunk<W> c;
     c.v = v;
     if (W == 16) {
         int64_t d, rem;
-        locate(a, nodes, P, d, rem, h);
-        *reinterpret_cast<uint4 *>(a.user_out + d) = c.v;
+        locate(op, nodes, blob, P, d, rem, h);
+        *reinterpret_cast<uint4 *>(op.user_out + d) = c.v;
         return;
     }
     int64_t d = 0, rem = 0;
 #pragma unroll
     for (int s = 0; s < 16 / W; s++) {
         if (s * W < nb) {
-            if (rem <= 0) locate(a, nodes, P + s * W, d, rem, h);
-            stw<W>(a.user_out + d, c.w[s]);
+            if (rem <= 0) locate(op, nodes, blob, P + s * W, d, rem, h);
+            stw<W>(op.user_out + d, c.w[s]);
             d += W;
             rem -= W;
         }
@@ -179,38 +204,114 @@ __device__ __forceinline__ void store_packed(char *p, uint4 v, int nb)
         if (s * W < nb) stw<W>(p + s * W, c.w[s]);
 }
 
+// One warp step: chunks [base, base + kStep) clipped to `end`.
 template <int W, bool PACK, bool PK16>
-__global__ void __launch_bounds__(kThreads) move_kernel(MoveArgs a)
+__device__ __forceinline__ void warp_step(const Op &op, const DNode *nodes, const char *blob, int64_t base,
+                                          int64_t end, int lane, Hint *h)
 {
-    __shared__ DNode snodes[kMaxSmemNodes];
-    const DNode *nodes = stage_nodes(a.blob, a.nnodes, snodes);
+    uint4 v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; u++) {
+        int64_t c = base + u * 32 + lane;
+        if (c < end) {
+            int64_t P = c * 16;
+            int nb = (int)(op.total - P < 16 ? op.total - P : 16);
+            if (PACK) v[u] = gather_chunk<W>(op, nodes, blob, P, nb, h[u]);
+            else v[u] = load_packed<W, PK16>(op.packed_in + P, nb);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; u++) {
+        int64_t c = base + u * 32 + lane;
+        if (c < end) {
+            int64_t P = c * 16;
+            int nb = (int)(op.total - P < 16 ? op.total - P : 16);
+            if (PACK) store_packed<W, PK16>(op.packed_out + P, v[u], nb);
+            else scatter_chunk<W>(op, nodes, blob, P, nb, v[u], h[u]);
+        }
+    }
+}
+
+template <int W, bool PACK, bool PK16>
+__global__ void __launch_bounds__(kThreads) move_kernel(Desc d, Op op, int64_t nchunks, int64_t per_warp)
+{
+    extern __shared__ uint4 smem[];
+    const char *blob;
+    const DNode *nodes;
+    stage_desc(d, smem, blob, nodes);
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
-    const int64_t c0 = warp * a.per_warp;
-    const int64_t c1 = min(c0 + a.per_warp, a.nchunks);
-    Hint h{-1, 0};
-    for (int64_t base = c0; base < c1; base += 32 * kU) {
-        uint4 v[kU];
+    const int64_t c0 = warp * per_warp;
+    const int64_t c1 = min(c0 + per_warp, nchunks);
+    Hint h[kU];
 #pragma unroll
-        for (int u = 0; u < kU; u++) {
-            int64_t c = base + u * 32 + lane;
-            if (c < c1) {
-                int64_t P = c * 16;
-                int nb = (int)(a.total - P < 16 ? a.total - P : 16);
-                if (PACK) v[u] = gather_chunk<W>(a, nodes, P, nb, h);
-                else v[u] = load_packed<W, PK16>(a.packed_in + P, nb);
-            }
-        }
+    for (int u = 0; u < kU; u++) h[u] = Hint{-1, 0};
+    for (int64_t base = c0; base < c1; base += kStep) warp_step<W, PACK, PK16>(op, nodes, blob, base, c1, lane, h);
+}
+
+// ---------------------------------------------------------------------------
+// batched movement: one persistent launch over many independent operations
+// ---------------------------------------------------------------------------
+struct BatchOp {
+    Desc d;
+    Op op;
+    int64_t nchunks;
+    int32_t wsel;   // word-size variant (see wsel_of)
+    int32_t pad_;
+};
+
+__host__ __device__ constexpr int wsel_of(int W, bool pk16)
+{
+    return W == 16 ? 0 : W == 8 ? (pk16 ? 1 : 2) : W == 4 ? (pk16 ? 3 : 4) : W == 2 ? (pk16 ? 5 : 6)
+                                                                                 : (pk16 ? 7 : 8);
+}
+
+// One launch per copy-word class present in a batch: ops are grouped by
+// (W, packed side 16-aligned) so each kernel is specialised like move_kernel.
+// tile0: nops+1 prefix of 2 KiB tiles per op of the group.  Warp w handles
+// tiles [w*tiles_per_warp, (w+1)*tiles_per_warp) in order.
+template <int W, bool PACK, bool PK16>
+__global__ void __launch_bounds__(kThreads) batch_kernel(const BatchOp *ops, const int64_t *tile0, int64_t nops,
+                                                         int64_t ntiles, int64_t tiles_per_warp)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int64_t t0 = warp * tiles_per_warp;
+    const int64_t t1 = min(t0 + tiles_per_warp, ntiles);
+    Hint oh{-1, 0};
+    Hint h[kU];
+    int64_t cur = -1;
+    for (int64_t t = t0; t < t1; t++) {
+        int64_t i = find_le(tile0, nops, t, oh, 0);
+        if (i != cur) {
 #pragma unroll
-        for (int u = 0; u < kU; u++) {
-            int64_t c = base + u * 32 + lane;
-            if (c < c1) {
-                int64_t P = c * 16;
-                int nb = (int)(a.total - P < 16 ? a.total - P : 16);
-                if (PACK) store_packed<W, PK16>(a.packed_out + P, v[u], nb);
-                else scatter_chunk<W>(a, nodes, P, nb, v[u], h);
-            }
+            for (int u = 0; u < kU; u++) h[u] = Hint{-1, 0};
+            cur = i;
         }
+        const BatchOp *b = ops + i;
+        const char *blob = b->d.blob;
+        const DNode *nodes = reinterpret_cast<const DNode *>(blob + sizeof(BlobHeader));
+        const Op op = b->op;
+        int64_t base = (t - tile0[i]) * kStep;
+        warp_step<W, PACK, PK16>(op, nodes, blob, base, b->nchunks, lane, h);
+    }
+}
+
+typedef void (*BatchKernel)(const BatchOp *, const int64_t *, int64_t, int64_t, int64_t);
+
+template <bool PACK>
+static BatchKernel pick_batch(int wsel)
+{
+    switch (wsel) {
+    case 0: return batch_kernel<16, PACK, true>;
+    case 1: return batch_kernel<8, PACK, true>;
+    case 2: return batch_kernel<8, PACK, false>;
+    case 3: return batch_kernel<4, PACK, true>;
+    case 4: return batch_kernel<4, PACK, false>;
+    case 5: return batch_kernel<2, PACK, true>;
+    case 6: return batch_kernel<2, PACK, false>;
+    case 7: return batch_kernel<1, PACK, true>;
+    default: return batch_kernel<1, PACK, false>;
     }
 }
 
@@ -218,7 +319,6 @@ __global__ void __launch_bounds__(kThreads) move_kernel(MoveArgs a)
 // segment enumeration (§3.1 MPIX_Type_iov, device form)
 // ---------------------------------------------------------------------------
 struct IovArgs {
-    const char *blob;
     dte_iov *out;
     int64_t *actual;
     const char *base;
@@ -228,14 +328,14 @@ struct IovArgs {
     FastDiv div_nseg;
     int64_t extent;
     int64_t per_warp;
-    int root;
-    int nnodes;
 };
 
-__global__ void __launch_bounds__(kThreads) iov_kernel(IovArgs a)
+__global__ void __launch_bounds__(kThreads) iov_kernel(Desc d, IovArgs a)
 {
-    __shared__ DNode snodes[kMaxSmemNodes];
-    const DNode *nodes = stage_nodes(a.blob, a.nnodes, snodes);
+    extern __shared__ uint4 smem[];
+    const char *blob;
+    const DNode *nodes;
+    stage_desc(d, smem, blob, nodes);
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int64_t k0 = warp * a.per_warp;
@@ -244,10 +344,10 @@ __global__ void __launch_bounds__(kThreads) iov_kernel(IovArgs a)
     for (int64_t k = k0 + lane; k < k1; k += 32) {
         int64_t s = a.first + k;
         int64_t e = fdiv(s, a.div_nseg);
-        int64_t d = e * a.extent, len = 0;
-        decode_seg(nodes, a.blob, a.root, s - e * a.nseg, d, len, h);
+        int64_t dd = e * a.extent, len = 0;
+        decode_seg(nodes, blob, d.root, s - e * a.nseg, dd, len, h);
         dte_iov v;
-        v.iov_base = (void *)(a.base + d);
+        v.iov_base = (void *)(a.base + dd);
         v.iov_len = len;
         a.out[k] = v;
     }
@@ -255,11 +355,14 @@ __global__ void __launch_bounds__(kThreads) iov_kernel(IovArgs a)
 }
 
 // §3.1 MPIX_Type_iov_len for a batch of budgets
-__global__ void __launch_bounds__(kThreads) iov_len_kernel(const char *blob, int root, int64_t nq,
-                                                           const int64_t *budget, int64_t *out_len,
-                                                           int64_t *out_bytes, int64_t size, int64_t nseg)
+__global__ void __launch_bounds__(kThreads) iov_len_kernel(Desc d, int64_t nq, const int64_t *budget,
+                                                           int64_t *out_len, int64_t *out_bytes, int64_t size,
+                                                           int64_t nseg)
 {
-    const DNode *nodes = reinterpret_cast<const DNode *>(blob + sizeof(BlobHeader));
+    extern __shared__ uint4 smem[];
+    const char *blob;
+    const DNode *nodes;
+    stage_desc(d, smem, blob, nodes);
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq;
          q += (int64_t)gridDim.x * blockDim.x) {
         int64_t B = budget[q];
@@ -271,7 +374,7 @@ __global__ void __launch_bounds__(kThreads) iov_len_kernel(const char *blob, int
             k = nseg;
             st = size;
         } else {
-            decode_pos(nodes, blob, root, B, k, st);
+            decode_pos(nodes, blob, d.root, B, k, st);
         }
         out_len[q] = k;
         out_bytes[q] = st;
@@ -279,12 +382,14 @@ __global__ void __launch_bounds__(kThreads) iov_len_kernel(const char *blob, int
 }
 
 // byte offset -> first segment index and count (first pass of iov_at_bytes)
-__global__ void __launch_bounds__(kThreads) at_bytes_first_kernel(const char *blob, int root, int64_t nq,
-                                                                  const int64_t *off, int64_t maxlen,
-                                                                  int64_t *first, int64_t *actual,
-                                                                  int64_t size, int64_t nseg)
+__global__ void __launch_bounds__(kThreads) at_bytes_first_kernel(Desc d, int64_t nq, const int64_t *off,
+                                                                  int64_t maxlen, int64_t *first,
+                                                                  int64_t *actual, int64_t size, int64_t nseg)
 {
-    const DNode *nodes = reinterpret_cast<const DNode *>(blob + sizeof(BlobHeader));
+    extern __shared__ uint4 smem[];
+    const char *blob;
+    const DNode *nodes;
+    stage_desc(d, smem, blob, nodes);
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq;
          q += (int64_t)gridDim.x * blockDim.x) {
         int64_t B = off[q];
@@ -294,20 +399,21 @@ __global__ void __launch_bounds__(kThreads) at_bytes_first_kernel(const char *bl
             continue;
         }
         int64_t k, st;
-        decode_pos(nodes, blob, root, B, k, st);
+        decode_pos(nodes, blob, d.root, B, k, st);
         first[q] = k;
         actual[q] = min(maxlen, nseg - k);
     }
 }
 
-__global__ void __launch_bounds__(kThreads) at_bytes_fill_kernel(const char *blob, int root, int nnodes,
-                                                                 int64_t nq, int64_t maxlen,
+__global__ void __launch_bounds__(kThreads) at_bytes_fill_kernel(Desc d, int64_t nq, int64_t maxlen,
                                                                  FastDiv div_max, const int64_t *first,
                                                                  const int64_t *actual, dte_iov *out,
                                                                  const char *base)
 {
-    __shared__ DNode snodes[kMaxSmemNodes];
-    const DNode *nodes = stage_nodes(blob, nnodes, snodes);
+    extern __shared__ uint4 smem[];
+    const char *blob;
+    const DNode *nodes;
+    stage_desc(d, smem, blob, nodes);
     Hint h{-1, 0};
     int64_t total = nq * maxlen;
     for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < total;
@@ -315,10 +421,10 @@ __global__ void __launch_bounds__(kThreads) at_bytes_fill_kernel(const char *blo
         int64_t q = fdiv(it, div_max);
         int64_t i = it - q * maxlen;
         if (i >= actual[q]) continue;
-        int64_t d = 0, len = 0;
-        decode_seg(nodes, blob, root, first[q] + i, d, len, h);
+        int64_t dd = 0, len = 0;
+        decode_seg(nodes, blob, d.root, first[q] + i, dd, len, h);
         dte_iov v;
-        v.iov_base = (void *)(base + d);
+        v.iov_base = (void *)(base + dd);
         v.iov_len = len;
         out[it] = v;
     }
@@ -327,27 +433,23 @@ __global__ void __launch_bounds__(kThreads) at_bytes_fill_kernel(const char *blo
 // ---------------------------------------------------------------------------
 // launch helpers
 // ---------------------------------------------------------------------------
-struct DevInfo {
-    int sms = 0;
-};
-
-static DevInfo &dev_info(int dev)
+static int sm_count(int dev)
 {
-    static DevInfo info[64];
-    DevInfo &d = info[dev & 63];
-    if (d.sms == 0) {
+    static int cache[64];
+    int &c = cache[dev & 63];
+    if (c == 0) {
         int v = 0;
         cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-        d.sms = v > 0 ? v : 1;
+        c = v > 0 ? v : 1;
     }
-    return d;
+    return c;
 }
 
 template <typename K>
-static int occupancy(K kernel)
+static int occupancy(K kernel, size_t smem)
 {
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, kThreads, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, kThreads, smem) != cudaSuccess ||
         blocks <= 0) {
         cudaGetLastError();
         blocks = 1;
@@ -355,18 +457,25 @@ static int occupancy(K kernel)
     return blocks;
 }
 
-typedef void (*MoveKernel)(MoveArgs);
-
-template <bool PACK>
-static MoveKernel pick_move(int W, bool pk16)
+static Desc make_desc(const Committed &c, const char *dblob, size_t *smem)
 {
-    switch (W) {
-    case 16: return move_kernel<16, PACK, true>;
-    case 8: return pk16 ? move_kernel<8, PACK, true> : move_kernel<8, PACK, false>;
-    case 4: return pk16 ? move_kernel<4, PACK, true> : move_kernel<4, PACK, false>;
-    case 2: return pk16 ? move_kernel<2, PACK, true> : move_kernel<2, PACK, false>;
-    default: return pk16 ? move_kernel<1, PACK, true> : move_kernel<1, PACK, false>;
+    Desc d;
+    d.blob = dblob;
+    d.blob_bytes = c.bytes;
+    d.root = c.root;
+    d.nnodes = c.nnodes;
+    d.pad_ = 0;
+    if (c.bytes <= kSmemBlob) {
+        d.stage = STAGE_BLOB;
+        *smem = (size_t)c.bytes;
+    } else if (c.nnodes <= kMaxSmemNodes) {
+        d.stage = STAGE_NODES;
+        *smem = (size_t)c.nnodes * sizeof(DNode);
+    } else {
+        d.stage = STAGE_NONE;
+        *smem = 0;
     }
+    return d;
 }
 
 static int64_t p2addr(const void *p)
@@ -385,55 +494,170 @@ static int64_t p2v(int64_t v)
     return low >= 16 ? 16 : (int64_t)low;
 }
 
-static int launch_move(bool pack, dte_type t, const char *blob, const void *user, void *packed, int64_t count,
+// copy word for one operation
+static int word_of(const Committed &c, int64_t extent, int64_t count, const void *user, const void *packed)
+{
+    int64_t W = std::min<int64_t>(c.align, std::min(p2addr(user), p2addr(packed)));
+    if (count > 1) W = std::min(W, p2v(extent));
+    return (int)W;
+}
+
+static Op make_op(const Committed &c, int64_t extent, const void *user, void *packed, int64_t count)
+{
+    Op op;
+    op.user_in = (const char *)user;
+    op.user_out = (char *)user;
+    op.packed_in = (const char *)packed;
+    op.packed_out = (char *)packed;
+    op.total = count * c.size;
+    op.esize = c.size;
+    op.extent = extent;
+    op.ediv = c.nodes()[c.root].div_size;
+    op.root = c.root;
+    op.pad_ = 0;
+    return op;
+}
+
+typedef void (*MoveKernel)(Desc, Op, int64_t, int64_t);
+
+template <bool PACK>
+static MoveKernel pick_move(int W, bool pk16)
+{
+    switch (W) {
+    case 16: return move_kernel<16, PACK, true>;
+    case 8: return pk16 ? move_kernel<8, PACK, true> : move_kernel<8, PACK, false>;
+    case 4: return pk16 ? move_kernel<4, PACK, true> : move_kernel<4, PACK, false>;
+    case 2: return pk16 ? move_kernel<2, PACK, true> : move_kernel<2, PACK, false>;
+    default: return pk16 ? move_kernel<1, PACK, true> : move_kernel<1, PACK, false>;
+    }
+}
+
+static int launch_move(bool pack, dte_type t, const char *dblob, const void *user, void *packed, int64_t count,
                        cudaStream_t stream, int dev)
 {
     Committed &c = *t->desc;
-    int64_t total = count * c.size;
-    if (total == 0) return DTE_SUCCESS;
-    int64_t W = std::min<int64_t>(c.align, std::min(p2addr(user), p2addr(packed)));
-    if (count > 1) W = std::min(W, p2v(t->extent()));
+    Op op = make_op(c, t->extent(), user, packed, count);
+    if (op.total == 0) return DTE_SUCCESS;
+    int W = word_of(c, t->extent(), count, user, packed);
     bool pk16 = p2addr(packed) >= 16;
-    MoveKernel k = pack ? pick_move<true>((int)W, pk16) : pick_move<false>((int)W, pk16);
-
-    static thread_local int occ_cache[64][2][5][2];
-    int wi = W == 16 ? 0 : W == 8 ? 1 : W == 4 ? 2 : W == 2 ? 3 : 4;
-    int &occ = occ_cache[dev & 63][pack ? 1 : 0][wi][pk16 ? 1 : 0];
-    if (occ == 0) occ = occupancy(k);
-
-    MoveArgs a;
-    a.blob = blob;
-    a.user_in = (const char *)user;
-    a.user_out = (char *)user;
-    a.packed_in = (const char *)packed;
-    a.packed_out = (char *)packed;
-    a.total = total;
-    a.esize = c.size;
-    a.extent = t->extent();
-    a.ediv = c.nodes()[c.root].div_size;  // divides by the element size
-    a.nchunks = (total + 15) / 16;
-    a.root = c.root;
-    a.nnodes = c.nnodes;
-    const int64_t step = 32 * kU;
-    int64_t warps_needed = (a.nchunks + step - 1) / step;
-    int64_t max_blocks = (int64_t)dev_info(dev).sms * occ;
-    int64_t blocks = std::min<int64_t>((warps_needed + kWarps - 1) / kWarps, max_blocks);
+    MoveKernel k = pack ? pick_move<true>(W, pk16) : pick_move<false>(W, pk16);
+    size_t smem = 0;
+    Desc d = make_desc(c, dblob, &smem);
+    // occupancy per (device, direction, variant, staging mode); the staged
+    // blob is sized for its upper bound
+    static thread_local int occ_cache[64][2][9][3];
+    int &occ = occ_cache[dev & 63][pack ? 1 : 0][wsel_of(W, pk16)][d.stage];
+    if (occ == 0) occ = occupancy(k, d.stage == STAGE_BLOB ? (size_t)kSmemBlob : smem);
+    int64_t nchunks = (op.total + 15) / 16;
+    int64_t steps = (nchunks + kStep - 1) / kStep;
+    int64_t max_blocks = (int64_t)sm_count(dev) * occ;
+    int64_t blocks = std::min<int64_t>((steps + kWarps - 1) / kWarps, max_blocks);
     if (blocks < 1) blocks = 1;
-    int64_t per_warp = (a.nchunks + blocks * kWarps - 1) / (blocks * kWarps);
-    per_warp = (per_warp + step - 1) / step * step;
-    a.per_warp = per_warp;
-    blocks = std::min<int64_t>(blocks, (a.nchunks + per_warp * kWarps - 1) / (per_warp * kWarps));
-    k<<<(unsigned)blocks, kThreads, 0, stream>>>(a);
+    int64_t per_warp = (steps + blocks * kWarps - 1) / (blocks * kWarps) * kStep;
+    blocks = (nchunks + per_warp * kWarps - 1) / (per_warp * kWarps);
+    k<<<(unsigned)blocks, kThreads, smem, stream>>>(d, op, nchunks, per_warp);
     if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
     return DTE_SUCCESS;
 }
 
-static int prep(dte_type t, const char **blob, int *dev)
+static bool capturing(dte_stream_t stream)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+// Resolve the device descriptor; frees finished deferred descriptors unless
+// the stream is being captured (no event polling inside a capture).
+static int prep(dte_type t, dte_stream_t stream, const char **blob, int *dev)
 {
     if (!handle_valid(t)) return DTE_ERR_TYPE;
     if (!t->committed) return DTE_ERR_TYPE;
-    reap_deferred();
+    if (!capturing(stream)) reap_deferred();
     return device_blob(t, blob, dev);
+}
+
+}  // namespace dte
+
+// ---------------------------------------------------------------------------
+// batches
+// ---------------------------------------------------------------------------
+namespace dte {
+struct BatchGroup {     // ops of one copy-word class, launched together
+    int wsel;
+    int64_t op0, nops;  // range in the (grouped) op table
+    int64_t t0;         // offset of this group's tile prefix in the prefix table
+    int64_t ntiles;
+    int occ;
+};
+}  // namespace dte
+
+struct dte_batch_s {
+    int kind = 0;  // DTE_BATCH_PACK or DTE_BATCH_UNPACK
+    int device = -1;
+    int64_t nops = 0, ntiles = 0;
+    char *dmem = nullptr;  // BatchOp[nops] followed by the groups' int64 tile prefixes
+    dte::BatchOp *d_ops = nullptr;
+    int64_t *d_tile0 = nullptr;
+    std::vector<dte::BatchGroup> groups;
+    std::vector<std::shared_ptr<dte::Committed>> keep;  // descriptors in use
+    std::vector<std::pair<void *, void *>> uses;        // (stream, event)
+    bool captured = false;
+    int blocks_per_sm = 0;          // 0: occupancy limit
+    int64_t tiles_per_warp_min = 1;
+};
+
+namespace dte {
+
+static std::mutex g_bmu;
+static std::vector<dte_batch> *g_bdeferred = new std::vector<dte_batch>();
+static std::vector<dte_batch> *g_blive = new std::vector<dte_batch>();
+
+static bool batch_idle(dte_batch b)
+{
+    if (b->captured) return false;
+    for (auto &u : b->uses)
+        if (cudaEventQuery((cudaEvent_t)u.second) == cudaErrorNotReady) return false;
+    return true;
+}
+
+static void batch_destroy(dte_batch b)
+{
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (b->device >= 0) cudaSetDevice(b->device);
+    for (auto &u : b->uses) cudaEventDestroy((cudaEvent_t)u.second);
+    if (b->dmem) cudaFree(b->dmem);
+    if (cur >= 0) cudaSetDevice(cur);
+    delete b;
+}
+
+static void reap_batches()
+{
+    std::vector<dte_batch> done;
+    {
+        std::lock_guard<std::mutex> g(g_bmu);
+        auto &v = *g_bdeferred;
+        for (size_t i = 0; i < v.size();) {
+            if (batch_idle(v[i])) {
+                done.push_back(v[i]);
+                v[i] = v.back();
+                v.pop_back();
+            } else {
+                i++;
+            }
+        }
+    }
+    for (auto b : done) batch_destroy(b);
+}
+
+static bool batch_valid(dte_batch b)
+{
+    std::lock_guard<std::mutex> g(g_bmu);
+    return b && std::find(g_blive->begin(), g_blive->end(), b) != g_blive->end();
 }
 
 }  // namespace dte
@@ -457,7 +681,7 @@ int dte_pack_enqueue(const void *inbuf, int64_t incount, dte_type type, void *ou
         if (!inbuf || !outbuf) return DTE_ERR_ARG;
         const char *blob;
         int dev;
-        if (int rc = prep(type, &blob, &dev)) return rc;
+        if (int rc = prep(type, stream, &blob, &dev)) return rc;
         int rc = launch_move(true, type, blob, inbuf, (char *)outbuf + *position, incount,
                              (cudaStream_t)stream, dev);
         if (rc) return rc;
@@ -487,7 +711,7 @@ int dte_unpack_enqueue(const void *inbuf, int64_t insize, int64_t *position, voi
         if (committed_overlaps(*type->desc, outcount, type->extent())) return DTE_ERR_OVERLAP;
         const char *blob;
         int dev;
-        if (int rc = prep(type, &blob, &dev)) return rc;
+        if (int rc = prep(type, stream, &blob, &dev)) return rc;
         int rc = launch_move(false, type, blob, outbuf, (char *)inbuf + *position, outcount,
                              (cudaStream_t)stream, dev);
         if (rc) return rc;
@@ -499,6 +723,192 @@ int dte_unpack_enqueue(const void *inbuf, int64_t insize, int64_t *position, voi
     } catch (...) {
         return DTE_ERR_NOMEM;
     }
+}
+
+int dte_batch_create(int kind, int64_t nops, const dte_op *ops, dte_batch *out)
+{
+    dte_batch b = nullptr;
+    try {
+        if (!out || nops < 0 || (nops > 0 && !ops)) return DTE_ERR_ARG;
+        if (kind != DTE_BATCH_PACK && kind != DTE_BATCH_UNPACK) return DTE_ERR_ARG;
+        reap_batches();
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) {
+            cudaGetLastError();
+            return DTE_ERR_NODEVICE;
+        }
+        std::vector<BatchOp> hops((size_t)nops);
+        b = new dte_batch_s();
+        b->kind = kind;
+        b->device = dev;
+        int rc = DTE_SUCCESS;
+        for (int64_t i = 0; i < nops && rc == DTE_SUCCESS; i++) {
+            const dte_op &o = ops[i];
+            BatchOp &h = hops[(size_t)i];
+            std::memset(&h, 0, sizeof h);
+            if (!handle_valid(o.type) || !o.type->committed) { rc = DTE_ERR_TYPE; break; }
+            if (o.count < 0) { rc = DTE_ERR_ARG; break; }
+            int64_t total;
+            if (__builtin_mul_overflow(o.count, o.type->size, &total)) { rc = DTE_ERR_OVERFLOW; break; }
+            if (total > 0) {
+                if (!o.user || !o.packed) { rc = DTE_ERR_ARG; break; }
+                if (kind == DTE_BATCH_UNPACK && committed_overlaps(*o.type->desc, o.count, o.type->extent())) {
+                    rc = DTE_ERR_OVERLAP;
+                    break;
+                }
+                const char *dblob;
+                int d2;
+                if ((rc = device_blob(o.type, &dblob, &d2)) != DTE_SUCCESS) break;
+                Committed &c = *o.type->desc;
+                size_t smem;
+                h.d = make_desc(c, dblob, &smem);
+                h.op = make_op(c, o.type->extent(), o.user, o.packed, o.count);
+                h.nchunks = (total + 15) / 16;
+                int W = word_of(c, o.type->extent(), o.count, o.user, o.packed);
+                h.wsel = wsel_of(W, p2addr(o.packed) >= 16);
+                b->keep.push_back(o.type->desc);
+            }
+        }
+        if (rc != DTE_SUCCESS) {
+            delete b;
+            return rc;
+        }
+        // group the non-empty ops by copy-word class, keeping their order
+        std::vector<BatchOp> grouped;
+        std::vector<int64_t> prefix;
+        grouped.reserve((size_t)nops);
+        for (int w = 0; w < 9; w++) {
+            BatchGroup g{w, (int64_t)grouped.size(), 0, (int64_t)prefix.size(), 0, 0};
+            prefix.push_back(0);
+            for (auto &h : hops) {
+                if (h.nchunks == 0 || h.wsel != w) continue;
+                grouped.push_back(h);
+                prefix.push_back(prefix.back() + (h.nchunks + kStep - 1) / kStep);
+            }
+            g.nops = (int64_t)grouped.size() - g.op0;
+            if (g.nops == 0) {
+                prefix.pop_back();
+                continue;
+            }
+            g.ntiles = prefix.back();
+            BatchKernel k = kind == DTE_BATCH_PACK ? pick_batch<true>(w) : pick_batch<false>(w);
+            g.occ = occupancy(k, 0);
+            b->groups.push_back(g);
+            b->ntiles += g.ntiles;
+        }
+        b->nops = (int64_t)grouped.size();
+        size_t ops_bytes = (grouped.size() * sizeof(BatchOp) + 15) & ~(size_t)15;
+        size_t bytes = ops_bytes + (prefix.size() + 1) * sizeof(int64_t);
+        if (cudaMalloc(&b->dmem, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            delete b;
+            return DTE_ERR_NOMEM;
+        }
+        b->d_ops = reinterpret_cast<BatchOp *>(b->dmem);
+        b->d_tile0 = reinterpret_cast<int64_t *>(b->dmem + ops_bytes);
+        if ((!grouped.empty() && cudaMemcpy(b->d_ops, grouped.data(), grouped.size() * sizeof(BatchOp),
+                                            cudaMemcpyHostToDevice) != cudaSuccess) ||
+            (!prefix.empty() && cudaMemcpy(b->d_tile0, prefix.data(), prefix.size() * sizeof(int64_t),
+                                           cudaMemcpyHostToDevice) != cudaSuccess)) {
+            batch_destroy(b);
+            return DTE_ERR_CUDA;
+        }
+        std::sort(b->keep.begin(), b->keep.end());
+        b->keep.erase(std::unique(b->keep.begin(), b->keep.end()), b->keep.end());
+        {
+            std::lock_guard<std::mutex> g(g_bmu);
+            g_blive->push_back(b);
+        }
+        *out = b;
+        return DTE_SUCCESS;
+    } catch (const Error &e) {
+        delete b;
+        return e.code;
+    } catch (...) {
+        delete b;
+        return DTE_ERR_NOMEM;
+    }
+}
+
+int dte_batch_set_launch(dte_batch batch, int blocks_per_sm, int64_t tiles_per_warp_min)
+{
+    if (!batch_valid(batch) || blocks_per_sm < 0 || tiles_per_warp_min < 1) return DTE_ERR_ARG;
+    batch->blocks_per_sm = blocks_per_sm;
+    batch->tiles_per_warp_min = tiles_per_warp_min;
+    return DTE_SUCCESS;
+}
+
+int dte_batch_enqueue(dte_batch b, dte_stream_t stream)
+{
+    if (!batch_valid(b)) return DTE_ERR_ARG;
+    if (b->ntiles == 0) return DTE_SUCCESS;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != b->device) return DTE_ERR_ARG;
+    for (const BatchGroup &g : b->groups) {
+        int per_sm = b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, g.occ) : g.occ;
+        int64_t max_blocks = (int64_t)sm_count(dev) * per_sm;
+        int64_t warps = std::min<int64_t>(max_blocks * kWarps,
+                                          (g.ntiles + b->tiles_per_warp_min - 1) / b->tiles_per_warp_min);
+        int64_t tpw = (g.ntiles + warps - 1) / warps;
+        int64_t blocks = ((g.ntiles + tpw - 1) / tpw + kWarps - 1) / kWarps;
+        BatchKernel k = b->kind == DTE_BATCH_PACK ? pick_batch<true>(g.wsel) : pick_batch<false>(g.wsel);
+        k<<<(unsigned)blocks, kThreads, 0, (cudaStream_t)stream>>>(b->d_ops + g.op0, b->d_tile0 + g.t0, g.nops,
+                                                                  g.ntiles, tpw);
+        if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
+    }
+    if (capturing(stream)) {
+        b->captured = true;
+        return DTE_SUCCESS;
+    }
+    for (auto &u : b->uses) {
+        if (u.first == (void *)stream) {
+            cudaEventRecord((cudaEvent_t)u.second, (cudaStream_t)stream);
+            return DTE_SUCCESS;
+        }
+    }
+    cudaEvent_t ev;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
+        cudaEventRecord(ev, (cudaStream_t)stream);
+        b->uses.push_back({(void *)stream, (void *)ev});
+    }
+    return DTE_SUCCESS;
+}
+
+int dte_batch_free(dte_batch *batch)
+{
+    if (!batch || !batch_valid(*batch)) return DTE_ERR_ARG;
+    dte_batch b = *batch;
+    bool idle;
+    {
+        std::lock_guard<std::mutex> g(g_bmu);
+        g_blive->erase(std::find(g_blive->begin(), g_blive->end(), b));
+        idle = batch_idle(b);
+        if (!idle) g_bdeferred->push_back(b);
+    }
+    if (idle) batch_destroy(b);
+    *batch = nullptr;
+    reap_batches();
+    return DTE_SUCCESS;
+}
+
+static int batch_once(int kind, int64_t nops, const dte_op *ops, dte_stream_t stream)
+{
+    dte_batch b = nullptr;
+    int rc = dte_batch_create(kind, nops, ops, &b);
+    if (rc) return rc;
+    rc = dte_batch_enqueue(b, stream);
+    int rc2 = dte_batch_free(&b);
+    return rc ? rc : rc2;
+}
+
+int dte_pack_batch_enqueue(int64_t nops, const dte_op *ops, dte_stream_t stream)
+{
+    return batch_once(DTE_BATCH_PACK, nops, ops, stream);
+}
+
+int dte_unpack_batch_enqueue(int64_t nops, const dte_op *ops, dte_stream_t stream)
+{
+    return batch_once(DTE_BATCH_UNPACK, nops, ops, stream);
 }
 
 int dte_type_iov_async(dte_type type, int64_t count, int64_t iov_offset, dte_iov *d_iov, int64_t max_iov_len,
@@ -515,15 +925,16 @@ int dte_type_iov_async(dte_type type, int64_t count, int64_t iov_offset, dte_iov
         int64_t n = iov_offset >= total ? 0 : std::min(max_iov_len, total - iov_offset);
         const char *blob;
         int dev;
-        if (int rc = prep(type, &blob, &dev)) return rc;
+        if (int rc = prep(type, stream, &blob, &dev)) return rc;
         if (n == 0) {
             if (d_actual_iov_len &&
                 cudaMemsetAsync(d_actual_iov_len, 0, sizeof(int64_t), (cudaStream_t)stream) != cudaSuccess)
                 return DTE_ERR_CUDA;
             return DTE_SUCCESS;
         }
+        size_t smem;
+        Desc d = make_desc(c, blob, &smem);
         IovArgs a;
-        a.blob = blob;
         a.out = d_iov;
         a.actual = d_actual_iov_len;
         a.base = (const char *)base;
@@ -532,15 +943,13 @@ int dte_type_iov_async(dte_type type, int64_t count, int64_t iov_offset, dte_iov
         a.nseg = c.nseg;
         a.div_nseg = c.nodes()[c.root].div_nseg;
         a.extent = type->extent();
-        a.root = c.root;
-        a.nnodes = c.nnodes;
         int64_t warps_needed = (n + 127) / 128;
-        int64_t max_blocks = (int64_t)dev_info(dev).sms * 8;
+        int64_t max_blocks = (int64_t)sm_count(dev) * 4;
         int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((warps_needed + kWarps - 1) / kWarps, max_blocks));
         int64_t per_warp = (n + blocks * kWarps - 1) / (blocks * kWarps);
         per_warp = (per_warp + 31) / 32 * 32;
         a.per_warp = per_warp;
-        iov_kernel<<<(unsigned)blocks, kThreads, 0, (cudaStream_t)stream>>>(a);
+        iov_kernel<<<(unsigned)blocks, kThreads, smem, (cudaStream_t)stream>>>(d, a);
         if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
         note_use(type, dev, stream);
         return DTE_SUCCESS;
@@ -561,11 +970,13 @@ int dte_type_iov_len_async(dte_type type, int64_t n, const int64_t *d_budget, in
         if (n == 0) return DTE_SUCCESS;
         const char *blob;
         int dev;
-        if (int rc = prep(type, &blob, &dev)) return rc;
+        if (int rc = prep(type, stream, &blob, &dev)) return rc;
         Committed &c = *type->desc;
-        int64_t blocks = std::min<int64_t>((n + kThreads - 1) / kThreads, (int64_t)dev_info(dev).sms * 8);
-        iov_len_kernel<<<(unsigned)blocks, kThreads, 0, (cudaStream_t)stream>>>(
-            blob, c.root, n, d_budget, d_iov_len, d_iov_bytes, c.size, c.nseg);
+        size_t smem;
+        Desc d = make_desc(c, blob, &smem);
+        int64_t blocks = std::min<int64_t>((n + kThreads - 1) / kThreads, (int64_t)sm_count(dev) * 4);
+        iov_len_kernel<<<(unsigned)blocks, kThreads, smem, (cudaStream_t)stream>>>(d, n, d_budget, d_iov_len,
+                                                                                  d_iov_bytes, c.size, c.nseg);
         if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
         note_use(type, dev, stream);
         return DTE_SUCCESS;
@@ -590,18 +1001,20 @@ int dte_type_iov_at_bytes_async(dte_type type, int64_t n, const int64_t *d_offse
         if (__builtin_mul_overflow(n, max_iov_len, &total)) return DTE_ERR_OVERFLOW;
         const char *blob;
         int dev;
-        if (int rc = prep(type, &blob, &dev)) return rc;
+        if (int rc = prep(type, stream, &blob, &dev)) return rc;
         Committed &c = *type->desc;
-        int64_t sms = dev_info(dev).sms;
-        int64_t b1 = std::min<int64_t>((n + kThreads - 1) / kThreads, sms * 8);
-        at_bytes_first_kernel<<<(unsigned)b1, kThreads, 0, (cudaStream_t)stream>>>(
-            blob, c.root, n, d_offset, max_iov_len, d_first, d_actual, c.size, c.nseg);
+        size_t smem;
+        Desc d = make_desc(c, blob, &smem);
+        int64_t sms = sm_count(dev);
+        int64_t b1 = std::min<int64_t>((n + kThreads - 1) / kThreads, sms * 4);
+        at_bytes_first_kernel<<<(unsigned)b1, kThreads, smem, (cudaStream_t)stream>>>(
+            d, n, d_offset, max_iov_len, d_first, d_actual, c.size, c.nseg);
         if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
         if (total > 0) {
             FastDiv dm = make_div(max_iov_len);
-            int64_t b2 = std::min<int64_t>((total + kThreads - 1) / kThreads, sms * 8);
-            at_bytes_fill_kernel<<<(unsigned)b2, kThreads, 0, (cudaStream_t)stream>>>(
-                blob, c.root, c.nnodes, n, max_iov_len, dm, d_first, d_actual, d_iov, (const char *)base);
+            int64_t b2 = std::min<int64_t>((total + kThreads - 1) / kThreads, sms * 4);
+            at_bytes_fill_kernel<<<(unsigned)b2, kThreads, smem, (cudaStream_t)stream>>>(
+                d, n, max_iov_len, dm, d_first, d_actual, d_iov, (const char *)base);
             if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
         }
         note_use(type, dev, stream);

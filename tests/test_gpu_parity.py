@@ -192,10 +192,14 @@ def test_halo_faces_small(n):
 
 
 def check_halo(n, g=2):
+    """Pack the six send faces (one struct, one launch) and unpack them into
+    the same six faces of a second grid.  The faces share edge cells, so as
+    one layout they overlap (rejected for unpack); as a batch of six per-face
+    unpacks each op is valid and shared cells receive identical bytes."""
     send = inputs.all_faces_struct(inputs.halo_face_specs(n, g))
-    recv = inputs.all_faces_struct(inputs.halo_recv_face_specs(n, g))
+    recv_faces = inputs.halo_face_specs(n, g)
     ts, os_ = both(send)
-    tr, or_ = both(recv)
+    tr, or_ = both(inputs.all_faces_struct(recv_faces))
     grid = inputs.normal_f64(n ** 3, 2).view(np.uint8)
     ref = os_.pack(grid, 1)
     d_grid = torch.from_numpy(grid).to(DEV)
@@ -203,11 +207,23 @@ def check_halo(n, g=2):
     s = torch.cuda.current_stream()
     dte.pack(d_grid, 1, ts, d_pk, 0, s)
     d_g2 = torch.full((grid.size,), SENT, dtype=torch.uint8, device=DEV)
-    dte.unpack(d_pk, 0, d_g2, 1, tr, s)
+    with pytest.raises(dte.DteError) as e:
+        dte.unpack(d_pk, 0, d_g2, 1, tr, s)
+    assert e.value.code == dte.ERR_OVERLAP
+    faces = [dte.Datatype.from_spec(f).commit() for f in recv_faces]
+    ops, pos = [], 0
+    for f in faces:
+        ops.append((f.h, 1, d_g2.data_ptr(), d_pk.data_ptr() + pos))
+        pos += f.size
+    dte.dte_unpack_batch_enqueue(ops, s.cuda_stream)
     s.synchronize()
     assert np.array_equal(d_pk.cpu().numpy(), ref)
     want = np.full(grid.size, SENT, np.uint8)
-    or_.unpack(ref, 1, want)
+    pos = 0
+    for spec in recv_faces:
+        of = oracle.from_spec(spec)
+        of.unpack(ref[pos:pos + of.size], 1, want)
+        pos += of.size
     assert np.array_equal(d_g2.cpu().numpy(), want)
 
 
@@ -326,3 +342,107 @@ def test_enqueue_errors():
     with pytest.raises(dte.DteError) as e:
         dte.dte_pack_enqueue(0, 1, t.h, buf.data_ptr(), 64, 0, 0)
     assert e.value.code == dte.ERR_ARG
+
+
+# --------------------------------------------------------------------------
+# batches (one persistent launch) and CUDA graph capture
+# --------------------------------------------------------------------------
+def make_batch_case(rng, nops, kind):
+    specs = [inputs.random_spec(rng, big=True) if i % 3 else inputs.sequential_spec(rng) for i in range(nops)]
+    cases = []
+    for spec in specs:
+        t, o = both(spec)
+        count = int(rng.integers(1, 3))
+        if o.size == 0 or (kind == dte.BATCH_UNPACK and o.overlaps(count)):
+            continue
+        lo, hi = span_of(o, count)
+        shift = int(rng.integers(0, 16))
+        cases.append(dict(t=t, o=o, count=count, base=-lo + shift, span=hi - lo + shift + 1))
+    return cases
+
+
+@pytest.mark.parametrize("kind", [1, 0])
+def test_batch_matches_oracle_and_per_call(kind):
+    rng = np.random.default_rng(301 + kind)
+    cases = make_batch_case(rng, 120, kind)
+    s = torch.cuda.current_stream()
+    ops, outs, refs = [], [], []
+    pk_total = sum(c["count"] * c["o"].size + 16 for c in cases)
+    d_pk = torch.full((pk_total,), SENT, dtype=torch.uint8, device=DEV)
+    pos = 0
+    for c in cases:
+        src = rng.integers(0, 256, c["span"], dtype=np.uint8)
+        c["src"] = src
+        ref = c["o"].pack(src, c["count"], c["base"])
+        if kind == dte.BATCH_PACK:
+            d_src = torch.from_numpy(src).to(DEV)
+            outs.append(d_src)
+            ops.append((c["t"].h, c["count"], d_src.data_ptr() + c["base"], d_pk.data_ptr() + pos))
+            refs.append((pos, ref))
+        else:
+            d_pk[pos:pos + ref.size] = torch.from_numpy(ref).to(DEV)
+            d_dst = torch.full((c["span"],), SENT, dtype=torch.uint8, device=DEV)
+            outs.append(d_dst)
+            ops.append((c["t"].h, c["count"], d_dst.data_ptr() + c["base"], d_pk.data_ptr() + pos))
+            want = np.full(c["span"], SENT, np.uint8)
+            c["o"].unpack(ref, c["count"], want, c["base"])
+            refs.append(want)
+        pos += ref.size + int(rng.integers(0, 17))
+    b = dte.Batch(kind, ops)
+    b.enqueue(s)
+    s.synchronize()
+    if kind == dte.BATCH_PACK:
+        got = d_pk.cpu().numpy()
+        for p, ref in refs:
+            assert np.array_equal(got[p:p + ref.size], ref)
+    else:
+        for d_dst, want in zip(outs, refs):
+            assert np.array_equal(d_dst.cpu().numpy(), want)
+    # replay the same batch under a CUDA graph: identical bytes
+    if kind == dte.BATCH_PACK:
+        d_pk.fill_(SENT)
+        g = torch.cuda.CUDAGraph()
+        gs = torch.cuda.Stream()
+        with torch.cuda.graph(g, stream=gs):
+            b.enqueue(gs)
+        for _ in range(2):
+            g.replay()
+        torch.cuda.synchronize()
+        got = d_pk.cpu().numpy()
+        for p, ref in refs:
+            assert np.array_equal(got[p:p + ref.size], ref)
+    b.free()
+
+
+def test_batch_rejects_bad_ops():
+    t = dte.Datatype.vector(4, 3, 2, dte.FLOAT32).commit()  # overlapping
+    buf = torch.zeros(256, dtype=torch.uint8, device=DEV)
+    with pytest.raises(dte.DteError) as e:
+        dte.dte_batch_create(dte.BATCH_UNPACK, [(t.h, 1, buf.data_ptr(), buf.data_ptr())])
+    assert e.value.code == dte.ERR_OVERLAP
+    u = dte.Datatype.vector(4, 1, 2, dte.FLOAT32)
+    with pytest.raises(dte.DteError) as e:
+        dte.dte_batch_create(dte.BATCH_PACK, [(u.h, 1, buf.data_ptr(), buf.data_ptr())])
+    assert e.value.code == dte.ERR_TYPE
+    with pytest.raises(dte.DteError):
+        dte.dte_batch_create(7, [])
+    b = dte.Batch(dte.BATCH_PACK, [])  # empty batch: enqueue is a no-op
+    b.enqueue()
+    b.free()
+
+
+def test_per_call_enqueue_under_graph_capture():
+    spec = ("vector", 1000, 2, 5, ("basic", "float64"))
+    t, o = both(spec)
+    span = o.true_lb + o.true_extent
+    src = inputs.random_bytes(span, 9)
+    d_src = torch.from_numpy(src).to(DEV)
+    d_pk = torch.empty(t.size, dtype=torch.uint8, device=DEV)
+    g = torch.cuda.CUDAGraph()
+    gs = torch.cuda.Stream()
+    with torch.cuda.graph(g, stream=gs):
+        dte.pack(d_src, 1, t, d_pk, 0, gs)
+    d_pk.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(d_pk.cpu().numpy(), o.pack(src, 1))
