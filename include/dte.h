@@ -271,9 +271,10 @@ enum dte_batch_kind { DTE_BATCH_UNPACK = 0, DTE_BATCH_PACK = 1 };
 DTE_API int dte_batch_create(int kind, int64_t nops, const dte_op *ops, dte_batch *out);
 
 /* Launch shape of a batch: at most blocks_per_sm CTAs of 256 threads per SM
- * (0 = as many as fit) and at least tiles_per_warp_min 2 KiB tiles per warp.
- * Used by the autotuner; the defaults are (0, 1). */
-DTE_API int dte_batch_set_launch(dte_batch batch, int blocks_per_sm, int64_t tiles_per_warp_min);
+ * (0 = as many as fit), and span_tiles consecutive 2 KiB tiles taken by a
+ * warp at a time (warps take spans round-robin).  Used by the autotuner;
+ * the defaults are (0, 1).  DTE_ERR_ARG for negative/zero values. */
+DTE_API int dte_batch_set_launch(dte_batch batch, int blocks_per_sm, int64_t span_tiles);
 
 /* Enqueue every operation of the batch as one kernel on `stream`.  Performs
  * no allocation or host copy, so it may be captured into a CUDA graph and

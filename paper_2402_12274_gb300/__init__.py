@@ -333,8 +333,8 @@ def dte_batch_create(kind: int, ops) -> int:
     return out.value
 
 
-def dte_batch_set_launch(batch: int, blocks_per_sm: int, tiles_per_warp_min: int = 1):
-    _ck(lib.dte_batch_set_launch(batch, blocks_per_sm, tiles_per_warp_min), "dte_batch_set_launch")
+def dte_batch_set_launch(batch: int, blocks_per_sm: int, span_tiles: int = 1):
+    _ck(lib.dte_batch_set_launch(batch, blocks_per_sm, span_tiles), "dte_batch_set_launch")
 
 
 def dte_batch_enqueue(batch: int, stream: int = 0):
@@ -365,8 +365,8 @@ class Batch:
     def enqueue(self, stream=None):
         dte_batch_enqueue(self.h, _stream_handle(stream))
 
-    def set_launch(self, blocks_per_sm: int, tiles_per_warp_min: int = 1):
-        dte_batch_set_launch(self.h, blocks_per_sm, tiles_per_warp_min)
+    def set_launch(self, blocks_per_sm: int, span_tiles: int = 1):
+        dte_batch_set_launch(self.h, blocks_per_sm, span_tiles)
 
     def free(self):
         if self.h:

@@ -232,8 +232,11 @@ __device__ __forceinline__ void warp_step(const Op &op, const DNode *nodes, cons
     }
 }
 
+// Warps take spans of `span` chunks (a multiple of kStep) round-robin, so
+// every warp sees every part of the layout (costly and cheap regions mix)
+// while a span keeps consecutive steps together for the search hints.
 template <int W, bool PACK, bool PK16>
-__global__ void __launch_bounds__(kThreads) move_kernel(Desc d, Op op, int64_t nchunks, int64_t per_warp)
+__global__ void __launch_bounds__(kThreads) move_kernel(Desc d, Op op, int64_t nchunks, int64_t span)
 {
     extern __shared__ uint4 smem[];
     const char *blob;
@@ -241,12 +244,15 @@ __global__ void __launch_bounds__(kThreads) move_kernel(Desc d, Op op, int64_t n
     stage_desc(d, smem, blob, nodes);
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
-    const int64_t c0 = warp * per_warp;
-    const int64_t c1 = min(c0 + per_warp, nchunks);
+    const int64_t stride = (int64_t)gridDim.x * kWarps * span;
     Hint h[kU];
 #pragma unroll
     for (int u = 0; u < kU; u++) h[u] = Hint{-1, 0};
-    for (int64_t base = c0; base < c1; base += kStep) warp_step<W, PACK, PK16>(op, nodes, blob, base, c1, lane, h);
+    for (int64_t c0 = warp * span; c0 < nchunks; c0 += stride) {
+        const int64_t c1 = min(c0 + span, nchunks);
+        for (int64_t base = c0; base < c1; base += kStep)
+            warp_step<W, PACK, PK16>(op, nodes, blob, base, c1, lane, h);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -268,32 +274,34 @@ __host__ __device__ constexpr int wsel_of(int W, bool pk16)
 
 // One launch per copy-word class present in a batch: ops are grouped by
 // (W, packed side 16-aligned) so each kernel is specialised like move_kernel.
-// tile0: nops+1 prefix of 2 KiB tiles per op of the group.  Warp w handles
-// tiles [w*tiles_per_warp, (w+1)*tiles_per_warp) in order.
+// tile0: nops+1 prefix of 2 KiB tiles per op of the group.  Warps take spans
+// of `span` consecutive tiles round-robin.
 template <int W, bool PACK, bool PK16>
 __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchOp *ops, const int64_t *tile0, int64_t nops,
-                                                         int64_t ntiles, int64_t tiles_per_warp)
+                                                         int64_t ntiles, int64_t span)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
-    const int64_t t0 = warp * tiles_per_warp;
-    const int64_t t1 = min(t0 + tiles_per_warp, ntiles);
+    const int64_t stride = (int64_t)gridDim.x * kWarps * span;
     Hint oh{-1, 0};
     Hint h[kU];
     int64_t cur = -1;
-    for (int64_t t = t0; t < t1; t++) {
-        int64_t i = find_le(tile0, nops, t, oh, 0);
-        if (i != cur) {
+    for (int64_t s0 = warp * span; s0 < ntiles; s0 += stride) {
+        const int64_t s1 = min(s0 + span, ntiles);
+        for (int64_t t = s0; t < s1; t++) {
+            int64_t i = find_le(tile0, nops, t, oh, 0);
+            if (i != cur) {
 #pragma unroll
-            for (int u = 0; u < kU; u++) h[u] = Hint{-1, 0};
-            cur = i;
+                for (int u = 0; u < kU; u++) h[u] = Hint{-1, 0};
+                cur = i;
+            }
+            const BatchOp *b = ops + i;
+            const char *blob = b->d.blob;
+            const DNode *nodes = reinterpret_cast<const DNode *>(blob + sizeof(BlobHeader));
+            const Op op = b->op;
+            int64_t base = (t - tile0[i]) * kStep;
+            warp_step<W, PACK, PK16>(op, nodes, blob, base, b->nchunks, lane, h);
         }
-        const BatchOp *b = ops + i;
-        const char *blob = b->d.blob;
-        const DNode *nodes = reinterpret_cast<const DNode *>(blob + sizeof(BlobHeader));
-        const Op op = b->op;
-        int64_t base = (t - tile0[i]) * kStep;
-        warp_step<W, PACK, PK16>(op, nodes, blob, base, b->nchunks, lane, h);
     }
 }
 
@@ -549,13 +557,15 @@ static int launch_move(bool pack, dte_type t, const char *dblob, const void *use
     int &occ = occ_cache[dev & 63][pack ? 1 : 0][wsel_of(W, pk16)][d.stage];
     if (occ == 0) occ = occupancy(k, d.stage == STAGE_BLOB ? (size_t)kSmemBlob : smem);
     int64_t nchunks = (op.total + 15) / 16;
-    int64_t steps = (nchunks + kStep - 1) / kStep;
+    // span: one step when the descriptor sits in shared memory; several when
+    // index tables are searched in global memory (consecutive steps reuse the
+    // search position)
+    int64_t span_steps = d.stage == STAGE_BLOB ? 1 : 8;
+    int64_t units = (nchunks + span_steps * kStep - 1) / (span_steps * kStep);
     int64_t max_blocks = (int64_t)sm_count(dev) * occ;
-    int64_t blocks = std::min<int64_t>((steps + kWarps - 1) / kWarps, max_blocks);
+    int64_t blocks = std::min<int64_t>((units + kWarps - 1) / kWarps, max_blocks);
     if (blocks < 1) blocks = 1;
-    int64_t per_warp = (steps + blocks * kWarps - 1) / (blocks * kWarps) * kStep;
-    blocks = (nchunks + per_warp * kWarps - 1) / (per_warp * kWarps);
-    k<<<(unsigned)blocks, kThreads, smem, stream>>>(d, op, nchunks, per_warp);
+    k<<<(unsigned)blocks, kThreads, smem, stream>>>(d, op, nchunks, span_steps * kStep);
     if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
     return DTE_SUCCESS;
 }
@@ -607,7 +617,7 @@ struct dte_batch_s {
     std::vector<std::pair<void *, void *>> uses;        // (stream, event)
     bool captured = false;
     int blocks_per_sm = 0;          // 0: occupancy limit
-    int64_t tiles_per_warp_min = 1;
+    int64_t span_tiles = 1;         // consecutive tiles a warp takes at a time
 };
 
 namespace dte {
@@ -830,11 +840,11 @@ int dte_batch_create(int kind, int64_t nops, const dte_op *ops, dte_batch *out)
     }
 }
 
-int dte_batch_set_launch(dte_batch batch, int blocks_per_sm, int64_t tiles_per_warp_min)
+int dte_batch_set_launch(dte_batch batch, int blocks_per_sm, int64_t span_tiles)
 {
-    if (!batch_valid(batch) || blocks_per_sm < 0 || tiles_per_warp_min < 1) return DTE_ERR_ARG;
+    if (!batch_valid(batch) || blocks_per_sm < 0 || span_tiles < 1) return DTE_ERR_ARG;
     batch->blocks_per_sm = blocks_per_sm;
-    batch->tiles_per_warp_min = tiles_per_warp_min;
+    batch->span_tiles = span_tiles;
     return DTE_SUCCESS;
 }
 
@@ -847,13 +857,12 @@ int dte_batch_enqueue(dte_batch b, dte_stream_t stream)
     for (const BatchGroup &g : b->groups) {
         int per_sm = b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, g.occ) : g.occ;
         int64_t max_blocks = (int64_t)sm_count(dev) * per_sm;
-        int64_t warps = std::min<int64_t>(max_blocks * kWarps,
-                                          (g.ntiles + b->tiles_per_warp_min - 1) / b->tiles_per_warp_min);
-        int64_t tpw = (g.ntiles + warps - 1) / warps;
-        int64_t blocks = ((g.ntiles + tpw - 1) / tpw + kWarps - 1) / kWarps;
+        int64_t span = b->span_tiles;
+        int64_t units = (g.ntiles + span - 1) / span;
+        int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((units + kWarps - 1) / kWarps, max_blocks));
         BatchKernel k = b->kind == DTE_BATCH_PACK ? pick_batch<true>(g.wsel) : pick_batch<false>(g.wsel);
         k<<<(unsigned)blocks, kThreads, 0, (cudaStream_t)stream>>>(b->d_ops + g.op0, b->d_tile0 + g.t0, g.nops,
-                                                                  g.ntiles, tpw);
+                                                                  g.ntiles, span);
         if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
     }
     if (capturing(stream)) {
