@@ -26,7 +26,9 @@ __all__ = [
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libdte.so")
+# DTE_LIBRARY selects another build of the same library (e.g. one compiled
+# with different tuning constants); default: the in-tree build.
+LIB_PATH = os.environ.get("DTE_LIBRARY") or os.path.join(_HERE, "libdte.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(

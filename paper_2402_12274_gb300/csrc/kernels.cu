@@ -39,7 +39,10 @@ namespace dte {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kU = 4;                 // chunks per lane per step
+#ifndef DTE_KU
+#define DTE_KU 4
+#endif
+constexpr int kU = DTE_KU;            // chunks per lane per step
 constexpr int kStep = 32 * kU;        // chunks per warp step (2 KiB)
 constexpr int64_t kSmemBlob = 16384;  // stage descriptors up to this size whole
 constexpr int kMaxSmemNodes = 64;
@@ -204,11 +207,53 @@ __device__ __forceinline__ void store_packed(char *p, uint4 v, int nb)
         if (s * W < nb) stw<W>(p + s * W, c.w[s]);
 }
 
+// One warp step, 16-byte words: a lane's chunks sit 512 bytes apart, so when
+// the run found for its first chunk extends past a later chunk, that chunk's
+// user address follows without walking the descriptor again.
+template <bool PACK>
+__device__ __forceinline__ void warp_step16(const Op &op, const DNode *nodes, const char *blob, int64_t base,
+                                            int64_t end, int lane, Hint *h)
+{
+    uint4 v[kU];
+    int64_t d[kU];
+    int64_t d0 = 0, rem0 = 0;
+#pragma unroll
+    for (int u = 0; u < kU; u++) {
+        int64_t c = base + u * 32 + lane;
+        if (c < end) {
+            if (u > 0 && rem0 >= (int64_t)u * 512 + 16) {
+                d[u] = d0 + u * 512;
+            } else {
+                int64_t rem;
+                locate(op, nodes, blob, c * 16, d[u], rem, h[u]);
+                if (u == 0) {
+                    d0 = d[u];
+                    rem0 = rem;
+                }
+            }
+            if (PACK) v[u] = __ldg(reinterpret_cast<const uint4 *>(op.user_in + d[u]));
+            else v[u] = __ldg(reinterpret_cast<const uint4 *>(op.packed_in + c * 16));
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; u++) {
+        int64_t c = base + u * 32 + lane;
+        if (c < end) {
+            if (PACK) *reinterpret_cast<uint4 *>(op.packed_out + c * 16) = v[u];
+            else *reinterpret_cast<uint4 *>(op.user_out + d[u]) = v[u];
+        }
+    }
+}
+
 // One warp step: chunks [base, base + kStep) clipped to `end`.
 template <int W, bool PACK, bool PK16>
 __device__ __forceinline__ void warp_step(const Op &op, const DNode *nodes, const char *blob, int64_t base,
                                           int64_t end, int lane, Hint *h)
 {
+    if (W == 16) {
+        warp_step16<PACK>(op, nodes, blob, base, end, lane, h);
+        return;
+    }
     uint4 v[kU];
 #pragma unroll
     for (int u = 0; u < kU; u++) {
