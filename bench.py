@@ -181,7 +181,7 @@ class L2Flush:
     def zero_(self):
         import torch
         self.w.zero_()
-        torch.sum(self.r, out=self.out)
+        torch.sum(self.r, dim=0, out=self.out)
 
 
 def dist_env():

@@ -308,7 +308,7 @@ struct BatchOp {
     Op op;
     int64_t nchunks;
     int32_t wsel;   // word-size variant (see wsel_of)
-    int32_t pad_;
+    int32_t soff;   // offset of the descriptor in the group's staged image, or -1
 };
 
 __host__ __device__ constexpr int wsel_of(int W, bool pk16)
@@ -320,11 +320,21 @@ __host__ __device__ constexpr int wsel_of(int W, bool pk16)
 // One launch per copy-word class present in a batch: ops are grouped by
 // (W, packed side 16-aligned) so each kernel is specialised like move_kernel.
 // tile0: nops+1 prefix of 2 KiB tiles per op of the group.  Warps take spans
-// of `span` consecutive tiles round-robin.
+// of `span` consecutive tiles round-robin.  When the group's descriptors fit
+// in shared memory together (`image`, image_bytes > 0) they are staged once
+// per CTA and every op with soff >= 0 walks its staged copy.
 template <int W, bool PACK, bool PK16>
 __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchOp *ops, const int64_t *tile0, int64_t nops,
-                                                         int64_t ntiles, int64_t span)
+                                                         int64_t ntiles, int64_t span, const char *image,
+                                                         int64_t image_bytes)
 {
+    extern __shared__ uint4 smem[];
+    if (image_bytes > 0) {
+        const uint4 *s = reinterpret_cast<const uint4 *>(image);
+        int nw = (int)(image_bytes / 16);
+        for (int i = threadIdx.x; i < nw; i += blockDim.x) smem[i] = s[i];
+        __syncthreads();
+    }
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int64_t stride = (int64_t)gridDim.x * kWarps * span;
@@ -341,7 +351,8 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchOp *ops, con
                 cur = i;
             }
             const BatchOp *b = ops + i;
-            const char *blob = b->d.blob;
+            const int soff = b->soff;
+            const char *blob = soff >= 0 ? reinterpret_cast<const char *>(smem) + soff : b->d.blob;
             const DNode *nodes = reinterpret_cast<const DNode *>(blob + sizeof(BlobHeader));
             const Op op = b->op;
             int64_t base = (t - tile0[i]) * kStep;
@@ -350,7 +361,7 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchOp *ops, con
     }
 }
 
-typedef void (*BatchKernel)(const BatchOp *, const int64_t *, int64_t, int64_t, int64_t);
+typedef void (*BatchKernel)(const BatchOp *, const int64_t *, int64_t, int64_t, int64_t, const char *, int64_t);
 
 template <bool PACK>
 static BatchKernel pick_batch(int wsel)
@@ -647,6 +658,8 @@ struct BatchGroup {     // ops of one copy-word class, launched together
     int64_t t0;         // offset of this group's tile prefix in the prefix table
     int64_t ntiles;
     int occ;
+    int64_t image_off;  // staged descriptor image (bytes into the batch image)
+    int64_t image_bytes;  // 0: descriptors are read from global memory
 };
 }  // namespace dte
 
@@ -657,6 +670,7 @@ struct dte_batch_s {
     char *dmem = nullptr;  // BatchOp[nops] followed by the groups' int64 tile prefixes
     dte::BatchOp *d_ops = nullptr;
     int64_t *d_tile0 = nullptr;
+    char *d_image = nullptr;
     std::vector<dte::BatchGroup> groups;
     std::vector<std::shared_ptr<dte::Committed>> keep;  // descriptors in use
     std::vector<std::pair<void *, void *>> uses;        // (stream, event)
@@ -793,6 +807,7 @@ int dte_batch_create(int kind, int64_t nops, const dte_op *ops, dte_batch *out)
             return DTE_ERR_NODEVICE;
         }
         std::vector<BatchOp> hops((size_t)nops);
+        std::vector<const Committed *> hc((size_t)nops, nullptr);
         b = new dte_batch_s();
         b->kind = kind;
         b->device = dev;
@@ -815,8 +830,10 @@ int dte_batch_create(int kind, int64_t nops, const dte_op *ops, dte_batch *out)
                 int d2;
                 if ((rc = device_blob(o.type, &dblob, &d2)) != DTE_SUCCESS) break;
                 Committed &c = *o.type->desc;
+                hc[(size_t)i] = &c;
                 size_t smem;
                 h.d = make_desc(c, dblob, &smem);
+                h.soff = -1;
                 h.op = make_op(c, o.type->extent(), o.user, o.packed, o.count);
                 h.nchunks = (total + 15) / 16;
                 int W = word_of(c, o.type->extent(), o.count, o.user, o.packed);
@@ -830,14 +847,18 @@ int dte_batch_create(int kind, int64_t nops, const dte_op *ops, dte_batch *out)
         }
         // group the non-empty ops by copy-word class, keeping their order
         std::vector<BatchOp> grouped;
+        std::vector<const Committed *> gc;
         std::vector<int64_t> prefix;
+        std::vector<char> image;  // staged descriptor images of all groups
         grouped.reserve((size_t)nops);
         for (int w = 0; w < 9; w++) {
-            BatchGroup g{w, (int64_t)grouped.size(), 0, (int64_t)prefix.size(), 0, 0};
+            BatchGroup g{w, (int64_t)grouped.size(), 0, (int64_t)prefix.size(), 0, 0, 0, 0};
             prefix.push_back(0);
-            for (auto &h : hops) {
+            for (size_t i = 0; i < hops.size(); i++) {
+                const BatchOp &h = hops[i];
                 if (h.nchunks == 0 || h.wsel != w) continue;
                 grouped.push_back(h);
+                gc.push_back(hc[i]);
                 prefix.push_back(prefix.back() + (h.nchunks + kStep - 1) / kStep);
             }
             g.nops = (int64_t)grouped.size() - g.op0;
@@ -846,14 +867,36 @@ int dte_batch_create(int kind, int64_t nops, const dte_op *ops, dte_batch *out)
                 continue;
             }
             g.ntiles = prefix.back();
+            // stage the group's distinct descriptors together if they fit
+            std::vector<std::pair<const Committed *, int64_t>> at;
+            int64_t img = 0;
+            for (int64_t i = g.op0; i < g.op0 + g.nops; i++) {
+                bool found = false;
+                for (auto &p : at) found = found || p.first == gc[(size_t)i];
+                if (!found) {
+                    at.push_back({gc[(size_t)i], img});
+                    img += (gc[(size_t)i]->bytes + 15) & ~(int64_t)15;
+                }
+                if (img > kSmemBlob) break;
+            }
+            if (img <= kSmemBlob) {
+                g.image_off = (int64_t)image.size();
+                g.image_bytes = img;
+                image.resize(image.size() + (size_t)img, 0);
+                for (auto &p : at) std::memcpy(image.data() + g.image_off + p.second, p.first->blob(), p.first->bytes);
+                for (int64_t i = g.op0; i < g.op0 + g.nops; i++)
+                    for (auto &p : at)
+                        if (p.first == gc[(size_t)i]) grouped[(size_t)i].soff = (int32_t)p.second;
+            }
             BatchKernel k = kind == DTE_BATCH_PACK ? pick_batch<true>(w) : pick_batch<false>(w);
-            g.occ = occupancy(k, 0);
+            g.occ = occupancy(k, (size_t)g.image_bytes);
             b->groups.push_back(g);
             b->ntiles += g.ntiles;
         }
         b->nops = (int64_t)grouped.size();
         size_t ops_bytes = (grouped.size() * sizeof(BatchOp) + 15) & ~(size_t)15;
-        size_t bytes = ops_bytes + (prefix.size() + 1) * sizeof(int64_t);
+        size_t pre_bytes = ((prefix.size() + 1) * sizeof(int64_t) + 15) & ~(size_t)15;
+        size_t bytes = ops_bytes + pre_bytes + image.size();
         if (cudaMalloc(&b->dmem, bytes) != cudaSuccess) {
             cudaGetLastError();
             delete b;
@@ -861,10 +904,13 @@ int dte_batch_create(int kind, int64_t nops, const dte_op *ops, dte_batch *out)
         }
         b->d_ops = reinterpret_cast<BatchOp *>(b->dmem);
         b->d_tile0 = reinterpret_cast<int64_t *>(b->dmem + ops_bytes);
+        b->d_image = b->dmem + ops_bytes + pre_bytes;
         if ((!grouped.empty() && cudaMemcpy(b->d_ops, grouped.data(), grouped.size() * sizeof(BatchOp),
                                             cudaMemcpyHostToDevice) != cudaSuccess) ||
             (!prefix.empty() && cudaMemcpy(b->d_tile0, prefix.data(), prefix.size() * sizeof(int64_t),
-                                           cudaMemcpyHostToDevice) != cudaSuccess)) {
+                                           cudaMemcpyHostToDevice) != cudaSuccess) ||
+            (!image.empty() &&
+             cudaMemcpy(b->d_image, image.data(), image.size(), cudaMemcpyHostToDevice) != cudaSuccess)) {
             batch_destroy(b);
             return DTE_ERR_CUDA;
         }
@@ -906,8 +952,8 @@ int dte_batch_enqueue(dte_batch b, dte_stream_t stream)
         int64_t units = (g.ntiles + span - 1) / span;
         int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((units + kWarps - 1) / kWarps, max_blocks));
         BatchKernel k = b->kind == DTE_BATCH_PACK ? pick_batch<true>(g.wsel) : pick_batch<false>(g.wsel);
-        k<<<(unsigned)blocks, kThreads, 0, (cudaStream_t)stream>>>(b->d_ops + g.op0, b->d_tile0 + g.t0, g.nops,
-                                                                  g.ntiles, span);
+        k<<<(unsigned)blocks, kThreads, (size_t)g.image_bytes, (cudaStream_t)stream>>>(
+            b->d_ops + g.op0, b->d_tile0 + g.t0, g.nops, g.ntiles, span, b->d_image + g.image_off, g.image_bytes);
         if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
     }
     if (capturing(stream)) {
