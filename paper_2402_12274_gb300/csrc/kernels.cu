@@ -44,6 +44,10 @@ constexpr int kWarps = kThreads / 32;
 #endif
 constexpr int kU = DTE_KU;            // chunks per lane per step
 constexpr int kStep = 32 * kU;        // chunks per warp step (2 KiB)
+#ifndef DTE_MINBLOCKS
+#define DTE_MINBLOCKS 4
+#endif
+constexpr int kMinBlocks = DTE_MINBLOCKS;  // CTAs per SM the data kernels are sized for (<= 64 regs)
 constexpr int64_t kSmemBlob = 16384;  // stage descriptors up to this size whole
 constexpr int kMaxSmemNodes = 64;
 
@@ -281,7 +285,7 @@ __device__ __forceinline__ void warp_step(const Op &op, const DNode *nodes, cons
 // every warp sees every part of the layout (costly and cheap regions mix)
 // while a span keeps consecutive steps together for the search hints.
 template <int W, bool PACK, bool PK16>
-__global__ void __launch_bounds__(kThreads) move_kernel(Desc d, Op op, int64_t nchunks, int64_t span)
+__global__ void __launch_bounds__(kThreads, kMinBlocks) move_kernel(Desc d, Op op, int64_t nchunks, int64_t span)
 {
     extern __shared__ uint4 smem[];
     const char *blob;
@@ -324,7 +328,7 @@ __host__ __device__ constexpr int wsel_of(int W, bool pk16)
 // in shared memory together (`image`, image_bytes > 0) they are staged once
 // per CTA and every op with soff >= 0 walks its staged copy.
 template <int W, bool PACK, bool PK16>
-__global__ void __launch_bounds__(kThreads) batch_kernel(const BatchOp *ops, const int64_t *tile0, int64_t nops,
+__global__ void __launch_bounds__(kThreads, kMinBlocks) batch_kernel(const BatchOp *ops, const int64_t *tile0, int64_t nops,
                                                          int64_t ntiles, int64_t span, const char *image,
                                                          int64_t image_bytes)
 {
@@ -354,9 +358,8 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchOp *ops, con
             const int soff = b->soff;
             const char *blob = soff >= 0 ? reinterpret_cast<const char *>(smem) + soff : b->d.blob;
             const DNode *nodes = reinterpret_cast<const DNode *>(blob + sizeof(BlobHeader));
-            const Op op = b->op;
             int64_t base = (t - tile0[i]) * kStep;
-            warp_step<W, PACK, PK16>(op, nodes, blob, base, b->nchunks, lane, h);
+            warp_step<W, PACK, PK16>(b->op, nodes, blob, base, b->nchunks, lane, h);
         }
     }
 }
