@@ -289,6 +289,35 @@ DTE_API int dte_batch_free(dte_batch *batch);
 DTE_API int dte_pack_batch_enqueue(int64_t nops, const dte_op *ops, dte_stream_t stream);
 DTE_API int dte_unpack_batch_enqueue(int64_t nops, const dte_op *ops, dte_stream_t stream);
 
+/* Largest nops accepted by dte_pack_batch_enqueue_noalloc. */
+#define DTE_NOALLOC_MAX_OPS 256
+
+/* Batched pack that allocates no device memory.  This entry point has no
+ * counterpart in the paper; it exists for callers that must not allocate
+ * while they enqueue work -- code whose device memory is already reserved in
+ * full by a caching allocator, latency-bound or signal-driven paths that
+ * cannot wait on the allocator, libraries handed a stream but not allowed to
+ * touch the device heap.  Same result as dte_pack_batch_enqueue.
+ *
+ * The op table goes into one fixed array of about 35 KB inside the library
+ * (held on every GPU that loads the library until the process exits)
+ * instead of memory from cudaMalloc.  Limits and rules:
+ *   - nops <= DTE_NOALLOC_MAX_OPS, else DTE_ERR_UNSUPPORTED (nothing queued);
+ *   - every type must be committed with the current device current (commit
+ *     uploads its descriptor; an op whose descriptor is not yet on this device
+ *     gives DTE_ERR_TYPE instead of an upload);
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) and should come before any stream capture;
+ *   - all calls on a device share the array and it keeps the last call's
+ *     table: two calls whose work overlaps on the GPU (different streams, or
+ *     a call issued before the previous one's kernels have read their table)
+ *     race -- serialise them on one stream.  The call writes every entry its
+ *     kernels read, so nothing needs clearing beforehand;
+ *   - the types must stay alive until the stream has executed the call (no
+ *     completion events are recorded, as creating them could allocate).
+ * Returns as soon as the work is queued on `stream`. */
+DTE_API int dte_pack_batch_enqueue_noalloc(int64_t nops, const dte_op *ops, dte_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

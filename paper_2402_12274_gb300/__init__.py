@@ -103,7 +103,9 @@ _SIGS = {
     "dte_batch_free": ([_pp], C.c_int),
     "dte_pack_batch_enqueue": ([_i64, C.POINTER(dte_op), _p], C.c_int),
     "dte_unpack_batch_enqueue": ([_i64, C.POINTER(dte_op), _p], C.c_int),
+    "dte_pack_batch_enqueue_noalloc": ([_i64, C.POINTER(dte_op), _p], C.c_int),
 }
+NOALLOC_MAX_OPS = 256  # DTE_NOALLOC_MAX_OPS in include/dte.h
 for _n, (_a, _r) in _SIGS.items():
     _f = getattr(lib, _n)
     _f.argtypes = _a
@@ -356,6 +358,13 @@ def dte_pack_batch_enqueue(ops, stream: int = 0):
 def dte_unpack_batch_enqueue(ops, stream: int = 0):
     arr, n = _ops_array(ops)
     _ck(lib.dte_unpack_batch_enqueue(n, arr, stream), "dte_unpack_batch_enqueue")
+
+
+def dte_pack_batch_enqueue_noalloc(ops, stream: int = 0):
+    """Batched pack into a fixed in-library op table (no device allocation);
+    see include/dte.h for its limits."""
+    arr, n = _ops_array(ops)
+    _ck(lib.dte_pack_batch_enqueue_noalloc(n, arr, stream), "dte_pack_batch_enqueue_noalloc")
 
 
 class Batch:

@@ -126,6 +126,8 @@ namespace dte {
 bool handle_valid(dte_type t);
 // Device copy of a committed type on the current device; uploads on first use.
 int device_blob(dte_type t, const char **out, int *device);
+// Device copy on device `dev` if already uploaded (never allocates).
+int device_blob_resident(dte_type t, int dev, const char **out);
 // Record that work using `t` was enqueued on `stream` (for deferred frees).
 void note_use(dte_type t, int device, void *stream);
 // Free device copies whose pending work has finished.

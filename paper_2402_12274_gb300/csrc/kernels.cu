@@ -1130,3 +1130,144 @@ int dte_type_iov_at_bytes_async(dte_type type, int64_t n, const int64_t *d_offse
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched pack that allocates nothing.
+//
+// For callers that must not allocate device memory while enqueueing work:
+// code running inside a memory budget that a caching allocator has already
+// reserved in full, real-time or signal-driven paths that cannot take the
+// allocator's locks or its latency, and libraries that are handed a stream
+// but forbidden to touch the device heap.  The regular batch keeps its op
+// table in memory it allocates with cudaMalloc; this variant writes the table
+// into a fixed array that is part of the library image instead.
+//
+// The array is `static __device__`: every GPU that loads the library holds
+// it until the process exits, and every call on a device shares it.  Host
+// code must not pass the array's name to a kernel (on the host that name is
+// only a stand-in), so its device address is looked up once per device with
+// cudaGetSymbolAddress -- on the first call made while that device is
+// current -- and that address is what the kernels receive.
+// ---------------------------------------------------------------------------
+namespace dte {
+
+constexpr int64_t kNoAllocMaxOps = DTE_NOALLOC_MAX_OPS;
+
+struct NoAllocTable {
+    BatchOp ops[kNoAllocMaxOps];
+    int64_t prefix[kNoAllocMaxOps + 9];  // per-group tile prefixes (<= 9 groups)
+};
+
+static __device__ __align__(256) char g_noalloc_scratch[sizeof(NoAllocTable)];
+
+static std::mutex g_noalloc_mu;
+static char *g_noalloc_addr[64];
+
+static int noalloc_scratch(int dev, char **out)
+{
+    if (dev < 0 || dev >= 64) return DTE_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return DTE_ERR_CUDA;
+        }
+        g_noalloc_addr[dev] = static_cast<char *>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return DTE_SUCCESS;
+}
+
+}  // namespace dte
+
+extern "C" int dte_pack_batch_enqueue_noalloc(int64_t nops, const dte_op *ops, dte_stream_t stream)
+{
+    try {
+        if (nops < 0 || (nops > 0 && !ops)) return DTE_ERR_ARG;
+        if (nops > kNoAllocMaxOps) return DTE_ERR_UNSUPPORTED;
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) {
+            cudaGetLastError();
+            return DTE_ERR_NODEVICE;
+        }
+        char *scratch = nullptr;
+        if (int rc = noalloc_scratch(dev, &scratch)) return rc;
+
+        // host image of the table: thread-local, so the call itself allocates nothing
+        static thread_local NoAllocTable table;
+        static thread_local BatchOp staged[kNoAllocMaxOps];
+        for (int64_t i = 0; i < nops; i++) {
+            const dte_op &o = ops[i];
+            BatchOp &h = staged[i];
+            std::memset(&h, 0, sizeof h);
+            if (!handle_valid(o.type) || !o.type->committed) return DTE_ERR_TYPE;
+            if (o.count < 0) return DTE_ERR_ARG;
+            int64_t total;
+            if (__builtin_mul_overflow(o.count, o.type->size, &total)) return DTE_ERR_OVERFLOW;
+            if (total == 0) continue;
+            if (!o.user || !o.packed) return DTE_ERR_ARG;
+            const char *dblob;
+            // the descriptor must already be on this device (commit uploads it)
+            if (int rc = device_blob_resident(o.type, dev, &dblob)) return rc;
+            Committed &c = *o.type->desc;
+            size_t smem;
+            h.d = make_desc(c, dblob, &smem);
+            h.soff = -1;
+            h.op = make_op(c, o.type->extent(), o.user, o.packed, o.count);
+            h.nchunks = (total + 15) / 16;
+            h.wsel = wsel_of(word_of(c, o.type->extent(), o.count, o.user, o.packed), p2addr(o.packed) >= 16);
+        }
+        // group by copy-word class exactly like the allocating batch
+        struct G { int wsel; int64_t op0, nops, t0, ntiles; };
+        G groups[9];
+        int ng = 0;
+        int64_t n = 0, np = 0;
+        for (int w = 0; w < 9; w++) {
+            G g{w, n, 0, np, 0};
+            table.prefix[np++] = 0;
+            for (int64_t i = 0; i < nops; i++) {
+                if (staged[i].nchunks == 0 || staged[i].wsel != w) continue;
+                table.ops[n++] = staged[i];
+                table.prefix[np] = table.prefix[np - 1] + (staged[i].nchunks + kStep - 1) / kStep;
+                np++;
+            }
+            g.nops = n - g.op0;
+            if (g.nops == 0) {
+                np--;
+                continue;
+            }
+            g.ntiles = table.prefix[np - 1];
+            groups[ng++] = g;
+        }
+        if (ng == 0) return DTE_SUCCESS;
+        BatchOp *d_ops = reinterpret_cast<BatchOp *>(scratch + offsetof(NoAllocTable, ops));
+        int64_t *d_prefix = reinterpret_cast<int64_t *>(scratch + offsetof(NoAllocTable, prefix));
+        // pageable source: the copy is staged before cudaMemcpyAsync returns,
+        // so the thread-local image may be rewritten by the next call
+        if (cudaMemcpyAsync(d_ops, table.ops, (size_t)n * sizeof(BatchOp), cudaMemcpyHostToDevice,
+                            (cudaStream_t)stream) != cudaSuccess ||
+            cudaMemcpyAsync(d_prefix, table.prefix, (size_t)np * sizeof(int64_t), cudaMemcpyHostToDevice,
+                            (cudaStream_t)stream) != cudaSuccess) {
+            cudaGetLastError();
+            return DTE_ERR_CUDA;
+        }
+        static thread_local int occ_cache[64][9];
+        for (int gi = 0; gi < ng; gi++) {
+            const G &g = groups[gi];
+            BatchKernel k = pick_batch<true>(g.wsel);
+            int &occ = occ_cache[dev & 63][g.wsel];
+            if (occ == 0) occ = occupancy(k, 0);
+            int64_t max_blocks = (int64_t)sm_count(dev) * occ;
+            int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((g.ntiles + kWarps - 1) / kWarps, max_blocks));
+            k<<<(unsigned)blocks, kThreads, 0, (cudaStream_t)stream>>>(d_ops + g.op0, d_prefix + g.t0, g.nops,
+                                                                      g.ntiles, 1, nullptr, 0);
+            if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
+        }
+        return DTE_SUCCESS;
+    } catch (const Error &e) {
+        return e.code;
+    } catch (...) {
+        return DTE_ERR_ARG;
+    }
+}

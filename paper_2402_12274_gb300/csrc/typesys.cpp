@@ -659,6 +659,19 @@ int device_blob(dte_type t, const char **out, int *device)
     return DTE_SUCCESS;
 }
 
+int device_blob_resident(dte_type t, int dev, const char **out)
+{
+    Committed &c = *t->desc;
+    std::lock_guard<std::mutex> g(c.mu);
+    for (auto &d : c.dev) {
+        if (d.device == dev) {
+            *out = d.ptr;
+            return DTE_SUCCESS;
+        }
+    }
+    return DTE_ERR_TYPE;
+}
+
 void note_use(dte_type t, int device, void *stream)
 {
     Committed &c = *t->desc;
