@@ -240,6 +240,21 @@ DTE_API int dte_pack_enqueue(const void *inbuf, int64_t incount, dte_type type, 
 DTE_API int dte_unpack_enqueue(const void *inbuf, int64_t insize, int64_t *position, void *outbuf,
                        int64_t outcount, dte_type type, dte_stream_t stream);
 
+/* Adjoint of a float32 pack (the backward of `packed = pack(x)` in a
+ * differentiable solver's halo gather; overlapping layouts are describable,
+ * §3): for every packed float k read from float src(k) of the user layout,
+ * gx[src(k)] += gy[k].  gy holds count*size/4 floats; gx is the user-layout
+ * origin (element e at gx + e*extent), both device pointers, 4-byte aligned,
+ * and every run of the type must be whole floats (DTE_ERR_ARG otherwise).
+ * Layouts without repeated bytes scatter-add one term per destination
+ * (bit-exact: gx + gy[k]).  Layouts that repeat bytes sum each
+ * destination's terms in packed order in FP64 and add the rounded sum
+ * (deterministic; the inverse is built on the host and uploaded on first use
+ * for a given (type, count, device) and cached with the type).  Enqueued on
+ * `stream`. */
+DTE_API int dte_pack_adjoint_f32_enqueue(const void *gy, int64_t count, dte_type type, void *gx,
+                                         dte_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Batches: many independent pack (or unpack) operations in one persistent
  * kernel launch.  The paper's motivation for stream-enqueued operations is

@@ -104,6 +104,7 @@ _SIGS = {
     "dte_pack_batch_enqueue": ([_i64, C.POINTER(dte_op), _p], C.c_int),
     "dte_unpack_batch_enqueue": ([_i64, C.POINTER(dte_op), _p], C.c_int),
     "dte_pack_batch_enqueue_noalloc": ([_i64, C.POINTER(dte_op), _p], C.c_int),
+    "dte_pack_adjoint_f32_enqueue": ([_p, _i64, _p, _p, _p], C.c_int),
 }
 NOALLOC_MAX_OPS = 256  # DTE_NOALLOC_MAX_OPS in include/dte.h
 for _n, (_a, _r) in _SIGS.items():
@@ -358,6 +359,11 @@ def dte_pack_batch_enqueue(ops, stream: int = 0):
 def dte_unpack_batch_enqueue(ops, stream: int = 0):
     arr, n = _ops_array(ops)
     _ck(lib.dte_unpack_batch_enqueue(n, arr, stream), "dte_unpack_batch_enqueue")
+
+
+def dte_pack_adjoint_f32_enqueue(gy: int, count: int, t: int, gx: int, stream: int = 0):
+    """gx[src(k)] += gy[k] for the float32 pack of `count` elements of t."""
+    _ck(lib.dte_pack_adjoint_f32_enqueue(gy, count, t, gx, stream), "dte_pack_adjoint_f32_enqueue")
 
 
 def dte_pack_batch_enqueue_noalloc(ops, stream: int = 0):

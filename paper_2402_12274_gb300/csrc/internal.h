@@ -81,7 +81,18 @@ struct DevCopy {
     bool captured = false;  // used under stream capture: never freed
 };
 
+// Inverse of a float32 pack over `count` elements (for the adjoint of layouts
+// that repeat entries): CSR by destination float, sources in packed order.
+struct AdjointInverse {
+    int device = -1;
+    int64_t count = 0;
+    int64_t ndest = 0;     // distinct destination floats
+    int64_t nsrc = 0;      // packed floats
+    char *dmem = nullptr;  // int64 rows[ndest+1], dest[ndest], cols[nsrc]
+};
+
 struct Committed {
+    std::vector<AdjointInverse> adj;  // cached inverses (device memory)
     std::vector<int64_t> storage;  // 8-byte aligned host blob
     int root = 0;
     int nnodes = 0;

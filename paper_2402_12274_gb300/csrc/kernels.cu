@@ -30,7 +30,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cstring>
+#include <numeric>
 #include <vector>
 
 #include "internal.h"
@@ -494,6 +496,77 @@ __global__ void __launch_bounds__(kThreads) at_bytes_fill_kernel(Desc d, int64_t
         v.iov_base = (void *)(base + dd);
         v.iov_len = len;
         out[it] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// adjoint of the typed float32 pack: gx[src(k)] += gy[k]
+// ---------------------------------------------------------------------------
+// Layouts without repeated bytes: every destination float receives exactly
+// one term, so a scatter with a float add (gx usually zero) reproduces the
+// adjoint exactly.  Same work split as move_kernel with 4-byte words.
+template <bool PK16>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) adjoint_kernel(Desc d, Op op, int64_t nchunks, int64_t span)
+{
+    extern __shared__ uint4 smem[];
+    const char *blob;
+    const DNode *nodes;
+    stage_desc(d, smem, blob, nodes);
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int64_t stride = (int64_t)gridDim.x * kWarps * span;
+    Hint h[kU];
+#pragma unroll
+    for (int u = 0; u < kU; u++) h[u] = Hint{-1, 0};
+    for (int64_t c0 = warp * span; c0 < nchunks; c0 += stride) {
+        const int64_t c1 = min(c0 + span, nchunks);
+        for (int64_t base = c0; base < c1; base += kStep) {
+            uint4 v[kU];
+#pragma unroll
+            for (int u = 0; u < kU; u++) {
+                int64_t c = base + u * 32 + lane;
+                if (c < c1) {
+                    int nb = (int)(op.total - c * 16 < 16 ? op.total - c * 16 : 16);
+                    v[u] = load_packed<4, PK16>(op.packed_in + c * 16, nb);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kU; u++) {
+                int64_t c = base + u * 32 + lane;
+                if (c < c1) {
+                    int64_t P = c * 16;
+                    int nb = (int)(op.total - P < 16 ? op.total - P : 16);
+                    Chunk<4> ch;
+                    ch.v = v[u];
+                    int64_t dd = 0, rem = 0;
+#pragma unroll
+                    for (int s = 0; s < 4; s++) {
+                        if (s * 4 < nb) {
+                            if (rem <= 0) locate(op, nodes, blob, P + s * 4, dd, rem, h[u]);
+                            float *p = reinterpret_cast<float *>(op.user_out + dd);
+                            *p = *p + __uint_as_float(ch.w[s]);
+                            dd += 4;
+                            rem -= 4;
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Layouts that repeat entries: one thread per destination float sums its
+// sources in packed order in FP64 (deterministic), then adds the rounded sum.
+__global__ void __launch_bounds__(kThreads) adjoint_csr_kernel(const int64_t *rows, const int64_t *dest,
+                                                               const int64_t *cols, int64_t ndest, const float *gy,
+                                                               float *gx)
+{
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < ndest;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int64_t j = rows[u]; j < rows[u + 1]; j++) s += (double)__ldg(gy + cols[j]);
+        float *p = gx + dest[u];
+        *p = *p + (float)s;
     }
 }
 
@@ -1269,5 +1342,128 @@ extern "C" int dte_pack_batch_enqueue_noalloc(int64_t nops, const dte_op *ops, d
         return e.code;
     } catch (...) {
         return DTE_ERR_ARG;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint of the typed float32 pack (differentiable halo gathers).
+// ---------------------------------------------------------------------------
+namespace dte {
+
+// Build (once per type, count and device) the destination-major inverse of
+// the pack: for every destination float the packed floats that read it, in
+// packed order.
+static int adjoint_inverse(dte_type t, int64_t count, int dev, AdjointInverse *out)
+{
+    Committed &c = *t->desc;
+    std::lock_guard<std::mutex> g(c.mu);
+    for (auto &a : c.adj) {
+        if (a.device == dev && a.count == count) {
+            *out = a;
+            return DTE_SUCCESS;
+        }
+    }
+    int64_t nsrc = count * (c.size / 4);
+    std::vector<int64_t> dst((size_t)nsrc);
+    int64_t p = 0;
+    Hint h{-1, 0};
+    const int64_t ext = t->extent();
+    for (int64_t e = 0; e < count; e++) {
+        for (int64_t k = 0; k < c.nseg; k++) {
+            int64_t d = 0, len = 0;
+            decode_seg(c.nodes(), c.blob(), c.root, k, d, len, h);
+            d += e * ext;
+            for (int64_t f = 0; f < len / 4; f++) dst[(size_t)p++] = d / 4 + f;
+        }
+    }
+    std::vector<int64_t> order((size_t)nsrc);
+    std::iota(order.begin(), order.end(), (int64_t)0);
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return dst[(size_t)a] < dst[(size_t)b]; });
+    std::vector<int64_t> rows, dest;
+    rows.reserve((size_t)nsrc + 1);
+    dest.reserve((size_t)nsrc);
+    for (int64_t j = 0; j < nsrc; j++) {
+        if (j == 0 || dst[(size_t)order[(size_t)j]] != dst[(size_t)order[(size_t)j - 1]]) {
+            rows.push_back(j);
+            dest.push_back(dst[(size_t)order[(size_t)j]]);
+        }
+    }
+    rows.push_back(nsrc);
+    AdjointInverse a;
+    a.device = dev;
+    a.count = count;
+    a.ndest = (int64_t)dest.size();
+    a.nsrc = nsrc;
+    size_t bytes = sizeof(int64_t) * (rows.size() + dest.size() + order.size());
+    if (cudaMalloc(&a.dmem, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return DTE_ERR_NOMEM;
+    }
+    char *q = a.dmem;
+    if (cudaMemcpy(q, rows.data(), rows.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(q + rows.size() * 8, dest.data(), dest.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(q + (rows.size() + dest.size()) * 8, order.data(), order.size() * 8, cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+        cudaFree(a.dmem);
+        return DTE_ERR_CUDA;
+    }
+    c.adj.push_back(a);
+    *out = a;
+    return DTE_SUCCESS;
+}
+
+}  // namespace dte
+
+extern "C" int dte_pack_adjoint_f32_enqueue(const void *gy, int64_t count, dte_type type, void *gx,
+                                            dte_stream_t stream)
+{
+    try {
+        if (!handle_valid(type)) return DTE_ERR_TYPE;
+        if (!type->committed) return DTE_ERR_TYPE;
+        if (count < 0) return DTE_ERR_ARG;
+        int64_t need;
+        if (__builtin_mul_overflow(count, type->size, &need)) return DTE_ERR_OVERFLOW;
+        if (need == 0) return DTE_SUCCESS;
+        if (!gy || !gx) return DTE_ERR_ARG;
+        Committed &c = *type->desc;
+        const int64_t ext = type->extent();
+        if (c.align < 4 || (count > 1 && ext % 4 != 0) || ((uintptr_t)gy & 3) || ((uintptr_t)gx & 3))
+            return DTE_ERR_ARG;
+        const char *blob;
+        int dev;
+        if (int rc = prep(type, stream, &blob, &dev)) return rc;
+        if (!committed_overlaps(c, count, ext)) {
+            Op op = make_op(c, ext, gx, const_cast<void *>(gy), count);
+            size_t smem;
+            Desc d = make_desc(c, blob, &smem);
+            bool pk16 = p2addr(gy) >= 16;
+            int64_t nchunks = (op.total + 15) / 16;
+            int64_t span_steps = d.stage == STAGE_BLOB ? 1 : 8;
+            int64_t units = (nchunks + span_steps * kStep - 1) / (span_steps * kStep);
+            auto k = pk16 ? adjoint_kernel<true> : adjoint_kernel<false>;
+            static thread_local int occ_cache[64][2][3];
+            int &occ = occ_cache[dev & 63][pk16 ? 1 : 0][d.stage];
+            if (occ == 0) occ = occupancy(k, d.stage == STAGE_BLOB ? (size_t)kSmemBlob : smem);
+            int64_t blocks = std::max<int64_t>(
+                1, std::min<int64_t>((units + kWarps - 1) / kWarps, (int64_t)sm_count(dev) * occ));
+            k<<<(unsigned)blocks, kThreads, smem, (cudaStream_t)stream>>>(d, op, nchunks, span_steps * kStep);
+        } else {
+            AdjointInverse a;
+            if (int rc = adjoint_inverse(type, count, dev, &a)) return rc;
+            const int64_t *rows = reinterpret_cast<const int64_t *>(a.dmem);
+            const int64_t *dest = rows + a.ndest + 1;
+            const int64_t *cols = dest + a.ndest;
+            int64_t blocks = std::max<int64_t>(
+                1, std::min<int64_t>((a.ndest + kThreads - 1) / kThreads, (int64_t)sm_count(dev) * 8));
+            adjoint_csr_kernel<<<(unsigned)blocks, kThreads, 0, (cudaStream_t)stream>>>(
+                rows, dest, cols, a.ndest, static_cast<const float *>(gy), static_cast<float *>(gx));
+        }
+        if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
+        note_use(type, dev, stream);
+        return DTE_SUCCESS;
+    } catch (const Error &e) {
+        return e.code;
+    } catch (...) {
+        return DTE_ERR_NOMEM;
     }
 }

@@ -377,18 +377,28 @@ FastDiv make_div(int64_t d)
 
 Committed::~Committed()
 {
+    bool captured = false;
+    for (auto &d : dev) captured = captured || d.captured;
+    int cur = -1;
+    if (!dev.empty()) cudaGetDevice(&cur);
     for (auto &d : dev) {
         if (!d.ptr || d.captured) continue;
-        int cur = -1;
-        cudaGetDevice(&cur);
         cudaSetDevice(d.device);
         for (auto &u : d.uses) {
             cudaEventSynchronize((cudaEvent_t)u.second);
             cudaEventDestroy((cudaEvent_t)u.second);
         }
         cudaFree(d.ptr);
-        if (cur >= 0) cudaSetDevice(cur);
     }
+    // adjoint inverses are used by the same enqueued work as the descriptor
+    if (!captured) {
+        for (auto &a : adj) {
+            if (!a.dmem) continue;
+            cudaSetDevice(a.device);
+            cudaFree(a.dmem);
+        }
+    }
+    if (cur >= 0) cudaSetDevice(cur);
 }
 
 std::shared_ptr<Committed> commit_node(const NP &root)
