@@ -48,6 +48,10 @@ def parse():
     p.add_argument("--impl", default="dte", choices=["dte", "reference"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--config", default="halo",
+                   help="halo (headline, default) | vector | records | batch | largeblock | autograd | all")
+    p.add_argument("--records-blocks", type=int, default=1 << 22)
+    p.add_argument("--batch-ops", type=int, default=10000)
     return p.parse_args()
 
 
@@ -404,10 +408,246 @@ def run_dte(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# Secondary workloads (one JSON line each; not the headline)
+# ---------------------------------------------------------------------------
+def _mean_s(stream, fn, reps, flush=None):
+    import torch
+    ev = []
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            fn()
+        for _ in range(reps):
+            if flush is not None:
+                flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            ev.append((a, b))
+    stream.synchronize()
+    return float(np.mean([a.elapsed_time(b) for a, b in ev])) * 1e-3
+
+
+def _line(name, metric, value, unit, extra):
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "higher_is_better": True,
+            "data": "synthetic", "config": {"workload": name}}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def run_config_vector(args):
+    """vector(1024,4,16) float32, count 64 (1 MiB packed out of a 4 MB span):
+    pack, unpack and the full 65,536-segment list, rotating over 64 buffer
+    pairs (256 MB > L2) so that every launch reads from HBM."""
+    import torch
+    import paper_2402_12274_gb300 as dte
+    from paper_2402_12274_gb300 import inputs
+    dev = torch.device("cuda", 0)
+    s = torch.cuda.Stream()
+    t = dte.Datatype.from_spec(inputs.strided_vector_spec()).commit()
+    count, span = 64, 63 * t.extent + t.true_extent
+    R = 64
+    srcs = [torch.from_numpy(inputs.uniform_f32(span // 4, 1 + i)).to(dev) for i in range(R)]
+    pks = [torch.empty(count * t.size, dtype=torch.uint8, device=dev) for _ in range(R)]
+    iov = torch.empty((count * 1024, 2), dtype=torch.int64, device=dev)
+    it = [0]
+
+    def pack():
+        i = it[0] = (it[0] + 1) % R
+        dte.dte_pack_enqueue(srcs[i].data_ptr(), count, t.h, pks[i].data_ptr(), pks[i].numel(), 0, s.cuda_stream)
+
+    def unpack():
+        i = it[0] = (it[0] + 1) % R
+        dte.dte_unpack_enqueue(pks[i].data_ptr(), pks[i].numel(), 0, srcs[i].data_ptr(), count, t.h, s.cuda_stream)
+
+    def iovq():
+        dte.dte_type_iov_async(t.h, count, 0, iov.data_ptr(), count * 1024, 0, 0, s.cuda_stream)
+
+    tp, tu, ti = _mean_s(s, pack, 400), _mean_s(s, unpack, 400), _mean_s(s, iovq, 400)
+    peak, _ = peaks()
+    z = count * t.size
+    _line("vector(1024,4,16) float32 x64 (1 MiB packed), 64 rotating buffers", "pack+unpack GB/s",
+          round(4 * z / (tp + tu) / 1e9, 1), "GB/s",
+          {"pack_GBs": round(2 * z / tp / 1e9, 1), "unpack_GBs": round(2 * z / tu / 1e9, 1),
+           "pack_us": round(tp * 1e6, 2), "unpack_us": round(tu * 1e6, 2),
+           "iov_segments_per_s": round(count * 1024 / ti), "iov_us": round(ti * 1e6, 2),
+           "hbm_peak_GBs": peak})
+
+
+def run_config_records(args):
+    """struct{int32[3],float64[5]} resized to 64 B inside an indexed type of
+    2^22 geometric blocks: pack/unpack GB/s, device iov chunk lookups from
+    random byte offsets (4096 segments each), host query latency."""
+    import torch
+    import paper_2402_12274_gb300 as dte
+    from paper_2402_12274_gb300 import inputs
+    dev = torch.device("cuda", 0)
+    s = torch.cuda.Stream()
+    nb = args.records_blocks
+    rng = np.random.default_rng(3)
+    t = dte.Datatype.from_spec(inputs.record_indexed_spec(rng, nb)).commit()
+    span = t.true_lb + t.true_extent
+    src = torch.empty(span, dtype=torch.uint8, device=dev)
+    src.random_(0, 256)
+    pk = torch.empty(t.size, dtype=torch.uint8, device=dev)
+    tp = _mean_s(s, lambda: dte.dte_pack_enqueue(src.data_ptr(), 1, t.h, pk.data_ptr(), pk.numel(), 0, s.cuda_stream), 10)
+    tu = _mean_s(s, lambda: dte.dte_unpack_enqueue(pk.data_ptr(), pk.numel(), 0, src.data_ptr(), 1, t.h, s.cuda_stream), 10)
+    nq, m = 4096, 4096
+    offs = torch.from_numpy(rng.integers(0, t.size, nq).astype(np.int64)).to(dev)
+    iov = torch.empty((nq * m, 2), dtype=torch.int64, device=dev)
+    first = torch.empty(nq, dtype=torch.int64, device=dev)
+    act = torch.empty(nq, dtype=torch.int64, device=dev)
+    tq = _mean_s(s, lambda: dte.dte_type_iov_at_bytes_async(t.h, nq, offs.data_ptr(), m, iov.data_ptr(), first.data_ptr(),
+                                                           act.data_ptr(), 0, s.cuda_stream), 10)
+    # host queries (the paper's synchronous API): iov_len(B) then iov(k, 4096)
+    import ctypes
+    buf = (dte.dte_iov * m)()
+    k, nbytes, got = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    lat = []
+    for b in rng.integers(0, t.size, 2000):
+        t0 = time.perf_counter()
+        dte.lib.dte_type_iov_len(t.h, int(b), ctypes.byref(k), ctypes.byref(nbytes))
+        dte.lib.dte_type_iov(t.h, k.value, buf, m, ctypes.byref(got))
+        lat.append(time.perf_counter() - t0)
+    peak, _ = peaks()
+    _line(f"record layout, {nb} indexed blocks ({t.size} B packed)", "pack+unpack GB/s",
+          round(4 * t.size / (tp + tu) / 1e9, 1), "GB/s",
+          {"pack_GBs": round(2 * t.size / tp / 1e9, 1), "unpack_GBs": round(2 * t.size / tu / 1e9, 1),
+           "descriptor_bytes": None, "iov_device_queries_per_s": round(nq / tq),
+           "iov_device_batch_us": round(tq * 1e6, 1),
+           "iov_host_query_p50_us": round(float(np.percentile(lat, 50)) * 1e6, 1),
+           "iov_host_query_p99_us": round(float(np.percentile(lat, 99)) * 1e6, 1), "hbm_peak_GBs": peak})
+
+
+def run_config_batch(args):
+    """10^4 independent packs (vector/indexed/subarray of float32 or bf16,
+    64 B - 4 MiB, seed 4): per-call launches vs one autotuned batch, each
+    also replayed from a captured CUDA graph.  Inputs total several GB (no
+    L2 flush needed)."""
+    import torch
+    import paper_2402_12274_gb300 as dte
+    from paper_2402_12274_gb300 import autotune, inputs
+    dev = torch.device("cuda", 0)
+    s = torch.cuda.Stream()
+    nops = args.batch_ops
+    rng = np.random.default_rng(4)
+    specs = inputs.batch_specs(rng, nops)
+    types = [dte.Datatype.from_spec(sp).commit() for sp, _ in specs]
+    spans = [t.true_lb + t.true_extent for t in types]
+    sizes = [t.size for t in types]
+    up = lambda v: (v + 255) // 256 * 256  # noqa: E731
+    so = np.concatenate([[0], np.cumsum([up(v) for v in spans])])
+    po = np.concatenate([[0], np.cumsum([up(v) for v in sizes])])
+    src = torch.empty(int(so[-1]), dtype=torch.uint8, device=dev)
+    src.random_(0, 256)
+    pk = torch.zeros(int(po[-1]), dtype=torch.uint8, device=dev)
+    ops = [(t.h, 1, src.data_ptr() + int(a), pk.data_ptr() + int(b)) for t, a, b in zip(types, so, po)]
+    total = int(sum(sizes))
+    sh = s.cuda_stream
+
+    def per_call():
+        for t, a, b, z in zip(types, so, po, sizes):
+            dte.dte_pack_enqueue(src.data_ptr() + int(a), 1, t.h, pk.data_ptr() + int(b), z, 0, sh)
+
+    batch = dte.Batch(dte.BATCH_PACK, ops)
+    shapes = [(16, z) for z in sizes]
+    best, _, table = autotune.tune(batch, dte.BATCH_PACK, shapes, stream=s, reps=3, use_cache=False)
+    t_batch = _mean_s(s, lambda: batch.enqueue(s), 10)
+    pk_b = pk.clone()
+    pk.zero_()
+    t_call = _mean_s(s, per_call, 3)
+    same = bool(torch.equal(pk, pk_b))
+
+    def graph_of(fn):
+        g = torch.cuda.CUDAGraph()
+        gs = torch.cuda.Stream()
+        with torch.cuda.graph(g, stream=gs):
+            fn(gs)
+        return g
+
+    g_batch = graph_of(lambda gs: batch.enqueue(gs))
+    g_call = graph_of(lambda gs: [dte.dte_pack_enqueue(src.data_ptr() + int(a), 1, t.h, pk.data_ptr() + int(b), z, 0,
+                                                       gs.cuda_stream) for t, a, b, z in zip(types, so, po, sizes)])
+    t_gb = _mean_s(s, g_batch.replay, 10)
+    t_gc = _mean_s(s, g_call.replay, 3)
+    peak, _ = peaks()
+    _line(f"{nops} independent packs, 64 B-4 MiB (vector/indexed/subarray, f32/bf16), {total} B packed",
+          "batched pack ops/s", round(nops / t_batch), "ops/s",
+          {"batch_GBs": round(2 * total / t_batch / 1e9, 1), "batch_ms": round(t_batch * 1e3, 3),
+           "per_call_ops_per_s": round(nops / t_call), "per_call_ms": round(t_call * 1e3, 3),
+           "graph_batch_ms": round(t_gb * 1e3, 3), "graph_per_call_ms": round(t_gc * 1e3, 3),
+           "speedup_batch_vs_per_call": round(t_call / t_batch, 2),
+           "speedup_graph_batch_vs_graph_per_call": round(t_gc / t_gb, 2),
+           "autotuned_launch": {"blocks_per_sm": best[0], "span_tiles": best[1]},
+           "autotune_table_ms": {f"{b}x{sp}": round(v * 1e3, 3) for (b, sp), v in (table or {}).items()},
+           "bit_identical_batch_vs_per_call": same, "hbm_peak_GBs": peak})
+
+
+def run_config_largeblock(args):
+    """Large-block pack/unpack: hvector of runs of 1 KiB - 1 MiB with gaps of
+    half a run, 256 MiB packed (the HBM-roofline gate), with torch's own
+    device copy of 256 MiB beside it."""
+    import torch
+    import paper_2402_12274_gb300 as dte
+    dev = torch.device("cuda", 0)
+    s = torch.cuda.Stream()
+    fl = L2Flush(dev)
+    dst = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    src = torch.empty((256 << 20) * 3 // 2 + (1 << 20), dtype=torch.uint8, device=dev)
+    res = {}
+    for L in (1024, 4096, 16384, 65536, 262144, 1 << 20):
+        n = (256 << 20) // L
+        t = dte.Datatype.hvector(n, 1, L + L // 2, dte.Datatype.contiguous(L // 8, dte.FLOAT64)).commit()
+        tp = _mean_s(s, lambda: dte.dte_pack_enqueue(src.data_ptr(), 1, t.h, dst.data_ptr(), dst.numel(), 0, s.cuda_stream), 30, fl)
+        tu = _mean_s(s, lambda: dte.dte_unpack_enqueue(dst.data_ptr(), dst.numel(), 0, src.data_ptr(), 1, t.h, s.cuda_stream), 30, fl)
+        res[str(L)] = {"pack_GBs": round(2 * t.size / tp / 1e9, 1), "unpack_GBs": round(2 * t.size / tu / 1e9, 1)}
+    tc = _mean_s(s, lambda: dst.copy_(src[: 256 << 20]), 30, fl)
+    peak, kind = peaks()
+    worst = min(v["pack_GBs"] for v in res.values())
+    _line("large-block hvector sweep, runs 1 KiB-1 MiB, 256 MiB packed", "large-block pack GB/s (min over runs)",
+          worst, "GB/s", {"frac_of_peak": round(worst / peak, 4), "peak": peak, "peak_source": kind,
+                          "runs": res, "torch_copy_GBs": round(2 * (256 << 20) / tc / 1e9, 1),
+                          "l2": "flushed between reps (write + read 512 MiB)"})
+
+
+def run_config_autograd(args):
+    """Differentiable pack of six halo faces of a 256^3 float32 field as
+    element-granular indexed types with 10% repeated entries: forward pack
+    and adjoint (deterministic segmented sum) times."""
+    import torch
+    import paper_2402_12274_gb300 as dte
+    from paper_2402_12274_gb300 import inputs
+    dev = torch.device("cuda", 0)
+    s = torch.cuda.Stream()
+    rng = np.random.default_rng(5)
+    n = 256
+    t = dte.Datatype.from_spec(inputs.all_faces_struct(inputs.halo_indexed_specs(rng, n, 2, 0.10))).commit()
+    x = torch.randn(n ** 3, dtype=torch.float32, device=dev)
+    y = torch.empty(t.size // 4, dtype=torch.float32, device=dev)
+    gx = torch.zeros_like(x)
+    fl = L2Flush(dev)
+    tf = _mean_s(s, lambda: dte.dte_pack_enqueue(x.data_ptr(), 1, t.h, y.data_ptr(), t.size, 0, s.cuda_stream), 50, fl)
+    tb = _mean_s(s, lambda: dte.dte_pack_adjoint_f32_enqueue(y.data_ptr(), 1, t.h, gx.data_ptr(), s.cuda_stream), 50, fl)
+    _line("six halo faces of 256^3 float32, indexed entries, 10% repeated", "forward+backward us",
+          round((tf + tb) * 1e6, 1), "us", {"higher_is_better": False, "forward_us": round(tf * 1e6, 1),
+                                            "backward_us": round(tb * 1e6, 1), "entries": t.size // 4})
+
+
+CONFIGS = {"vector": run_config_vector, "records": run_config_records, "batch": run_config_batch,
+           "largeblock": run_config_largeblock, "autograd": run_config_autograd}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config != "halo":
+        import torch
+        torch.cuda.set_device(0)
+        for name in (CONFIGS if args.config == "all" else args.config.split(",")):
+            CONFIGS[name](args)
     else:
         run_dte(args)
 

@@ -132,6 +132,11 @@ struct Hint {
 
 DTE_HD int64_t find_le(const int64_t *a, int64_t n, int64_t x, Hint &h, int node)
 {
+    // Short lists (a struct's members, a record's runs) are searched
+    // directly; the hint is kept for the large table on the path, which
+    // would otherwise be re-searched from the top after every visit to a
+    // short child list.
+    if (n <= 32) return bsearch_le(a, 0, n, x);
     if (h.node != node) {
         int64_t b = bsearch_le(a, 0, n, x);
         h.node = node;
@@ -300,12 +305,14 @@ DTE_HD void decode_pos(const DNode *nodes, const char *blob, int node, int64_t P
 }
 
 // ---------------------------------------------------------------------------
-// Merged segment index -> (displacement, length).  0 <= k < nseg.
+// Merged segment index -> (displacement, length, packed offset where the
+// segment starts).  0 <= k < nseg.
 // ---------------------------------------------------------------------------
 DTE_HD void decode_seg(const DNode *nodes, const char *blob, int node, int64_t k,
-                       int64_t &disp, int64_t &len, Hint &h)
+                       int64_t &disp, int64_t &len, int64_t &pstart, Hint &h)
 {
     int64_t ext = 0;
+    pstart = 0;
     for (;;) {
         const DNode &N = nodes[node];
         disp += N.base;
@@ -330,6 +337,7 @@ DTE_HD void decode_seg(const DNode *nodes, const char *blob, int node, int64_t k
                 j = k - i * C.nseg;
             }
             disp += i * N.stride;
+            pstart += i * C.size;
             k = j;
             node = N.child;
             continue;
@@ -339,6 +347,7 @@ DTE_HD void decode_seg(const DNode *nodes, const char *blob, int node, int64_t k
         if (N.flags & NF_RUNS) {
             b = k;
             disp += arr<int64_t>(blob, N.a_disp)[b];
+            pstart += pb[b];
             len = (pb[b + 1] - pb[b]) + ext;
             return;
         }
@@ -364,6 +373,7 @@ DTE_HD void decode_seg(const DNode *nodes, const char *blob, int node, int64_t k
         int64_t local = k - ps + ((ef & EF_MERGED_IN) ? 1 : 0);
         int64_t cnt = fdiv(pb[b + 1] - pb[b], C.div_size);
         disp += arr<int64_t>(blob, N.a_disp)[b];
+        pstart += pb[b];
         if (ef & EF_SINGLE) {
             if (N.a_tail) ext += arr<int64_t>(blob, N.a_tail)[b];
             disp += C.base;
@@ -388,9 +398,17 @@ DTE_HD void decode_seg(const DNode *nodes, const char *blob, int node, int64_t k
             j = local - i * C.nseg;
         }
         disp += i * stride;
+        pstart += i * C.size;
         k = j;
         node = child;
     }
+}
+
+DTE_HD void decode_seg(const DNode *nodes, const char *blob, int node, int64_t k,
+                       int64_t &disp, int64_t &len, Hint &h)
+{
+    int64_t pstart;
+    decode_seg(nodes, blob, node, k, disp, len, pstart, h);
 }
 
 }  // namespace dte

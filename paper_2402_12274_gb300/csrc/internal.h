@@ -43,6 +43,7 @@ struct Node {
     int64_t first_d = 0, first_len = 0, last_d = 0, last_len = 0;  // incl. base
     int64_t tlo = 0, thi = 0;  // byte bounds of the data, incl. base
     int64_t align = 16;        // power of two <= 16 dividing every offset/length
+    int64_t maxrun = 0;        // longest contiguous run a decode can return
     bool nonoverlap = true;    // proven: no byte appears twice
     // RUN
     int64_t len = 0;
@@ -98,6 +99,7 @@ struct Committed {
     int nnodes = 0;
     int64_t bytes = 0;
     int64_t align = 16;            // type alignment class (<= 16)
+    int64_t maxrun = 0;            // longest raw run of the descriptor
     int64_t nseg = 0, size = 0;
     bool nonoverlap = true;        // structural proof for one element
     int overlap_exact = -1;        // -1 unknown, 0 no, 1 yes (one element)

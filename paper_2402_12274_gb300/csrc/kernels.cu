@@ -51,6 +51,7 @@ constexpr int kStep = 32 * kU;        // chunks per warp step (2 KiB)
 #endif
 constexpr int kMinBlocks = DTE_MINBLOCKS;  // CTAs per SM the data kernels are sized for (<= 64 regs)
 constexpr int64_t kSmemBlob = 16384;  // stage descriptors up to this size whole
+constexpr int64_t kSegMaxRun = 256;   // segment-major kernel for runs up to this length
 constexpr int kMaxSmemNodes = 64;
 
 enum : int { STAGE_NONE = 0, STAGE_NODES = 1, STAGE_BLOB = 2 };
@@ -303,6 +304,75 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) move_kernel(Desc d, Op o
         const int64_t c1 = min(c0 + span, nchunks);
         for (int64_t base = c0; base < c1; base += kStep)
             warp_step<W, PACK, PK16>(op, nodes, blob, base, c1, lane, h);
+    }
+}
+
+// Segment-major movement for layouts of short runs moved in words of fewer
+// than 16 bytes.  Each lane walks the descriptor once per round for one whole
+// segment (a single convergent decode per lane instead of one per run end
+// inside a chunk), then the warp moves the packed range its 32 segments cover
+// together: lane l takes words l, l+32, l+64, l+96 of each 128-word slice and
+// finds the segment of each word with a 5-step shuffle search over the
+// lanes' packed start offsets, so packed-side accesses stay coalesced.
+template <int W, bool PACK>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) seg_kernel(Desc d, Op op, int64_t nseg_elem, FastDiv div_nseg,
+                                                                  int64_t nsegs, int64_t span)
+{
+    extern __shared__ uint4 smem[];
+    const char *blob;
+    const DNode *nodes;
+    stage_desc(d, smem, blob, nodes);
+    using T = typename Word<W>::T;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int64_t stride = (int64_t)gridDim.x * kWarps * span;
+    Hint h{-1, 0};
+    for (int64_t s0 = warp * span; s0 < nsegs; s0 += stride) {
+        const int64_t s1 = min(s0 + span, nsegs);
+        for (int64_t base = s0; base < s1; base += 32) {
+            const int nvalid = (int)min((int64_t)32, s1 - base);
+            int64_t disp = 0, len = 0, ps = 0;
+            if (lane < nvalid) {
+                const int64_t k = base + lane;
+                const int64_t e = fdiv(k, div_nseg);
+                disp = e * op.extent;
+                decode_seg(nodes, blob, op.root, k - e * nseg_elem, disp, len, ps, h);
+                ps += e * op.esize;
+            }
+            const int64_t p0 = __shfl_sync(FULL, ps, 0);
+            const int64_t p1 = __shfl_sync(FULL, ps + len, nvalid - 1);
+            const int64_t nwords = (p1 - p0) / W;
+            for (int64_t w0 = 0; w0 < nwords; w0 += 32 * kU) {
+                T v[kU];
+                int64_t ud[kU];
+#pragma unroll
+                for (int u = 0; u < kU; u++) {
+                    const int64_t wi = w0 + u * 32 + lane;
+                    const int64_t q = p0 + wi * W;
+                    int lo = 0;
+#pragma unroll
+                    for (int step = 16; step >= 1; step >>= 1) {
+                        const int cand = lo + step;
+                        const int64_t pc = __shfl_sync(FULL, ps, cand & 31);
+                        if (cand < nvalid && pc <= q) lo = cand;
+                    }
+                    ud[u] = __shfl_sync(FULL, disp, lo) + (q - __shfl_sync(FULL, ps, lo));
+                    if (wi < nwords) {
+                        if (PACK) v[u] = ldw<W>(op.user_in + ud[u]);
+                        else v[u] = ldw<W>(op.packed_in + q);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kU; u++) {
+                    const int64_t wi = w0 + u * 32 + lane;
+                    if (wi < nwords) {
+                        if (PACK) stw<W>(op.packed_out + p0 + wi * W, v[u]);
+                        else stw<W>(op.user_out + ud[u], v[u]);
+                    }
+                }
+            }
+        }
     }
 }
 
@@ -688,13 +758,39 @@ static int launch_move(bool pack, dte_type t, const char *dblob, const void *use
     static thread_local int occ_cache[64][2][9][3];
     int &occ = occ_cache[dev & 63][pack ? 1 : 0][wsel_of(W, pk16)][d.stage];
     if (occ == 0) occ = occupancy(k, d.stage == STAGE_BLOB ? (size_t)kSmemBlob : smem);
-    int64_t nchunks = (op.total + 15) / 16;
-    // span: one step when the descriptor sits in shared memory; several when
-    // index tables are searched in global memory (consecutive steps reuse the
-    // search position)
-    int64_t span_steps = d.stage == STAGE_BLOB ? 1 : 8;
-    int64_t units = (nchunks + span_steps * kStep - 1) / (span_steps * kStep);
     int64_t max_blocks = (int64_t)sm_count(dev) * occ;
+    int64_t max_warps = max_blocks * kWarps;
+    if (W < 16 && c.maxrun <= kSegMaxRun) {
+        // short runs, small words: one decode per segment, cooperative copy
+        typedef void (*SegKernel)(Desc, Op, int64_t, FastDiv, int64_t, int64_t);
+        SegKernel sk;
+        switch (W) {
+        case 8: sk = pack ? seg_kernel<8, true> : seg_kernel<8, false>; break;
+        case 4: sk = pack ? seg_kernel<4, true> : seg_kernel<4, false>; break;
+        case 2: sk = pack ? seg_kernel<2, true> : seg_kernel<2, false>; break;
+        default: sk = pack ? seg_kernel<1, true> : seg_kernel<1, false>; break;
+        }
+        static thread_local int socc_cache[64][2][4][3];
+        int &socc = socc_cache[dev & 63][pack ? 1 : 0][W == 8 ? 0 : W == 4 ? 1 : W == 2 ? 2 : 3][d.stage];
+        if (socc == 0) socc = occupancy(sk, d.stage == STAGE_BLOB ? (size_t)kSmemBlob : smem);
+        int64_t nsegs = count * c.nseg;
+        int64_t rounds = (nsegs + 31) / 32;
+        int64_t span_rounds = std::max<int64_t>(1, std::min<int64_t>(8, rounds / ((int64_t)sm_count(dev) * socc * kWarps)));
+        int64_t units = (rounds + span_rounds - 1) / span_rounds;
+        int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((units + kWarps - 1) / kWarps,
+                                                                (int64_t)sm_count(dev) * socc));
+        sk<<<(unsigned)blocks, kThreads, smem, stream>>>(d, op, c.nseg, c.nodes()[c.root].div_nseg, nsegs,
+                                                        32 * span_rounds);
+        if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
+        return DTE_SUCCESS;
+    }
+    int64_t nchunks = (op.total + 15) / 16;
+    // span: one step when the descriptor sits in shared memory; up to eight
+    // when index tables are searched in global memory (consecutive steps
+    // reuse the search position), but never so many that warps go idle
+    int64_t steps = (nchunks + kStep - 1) / kStep;
+    int64_t span_steps = d.stage == STAGE_BLOB ? 1 : std::max<int64_t>(1, std::min<int64_t>(8, steps / max_warps));
+    int64_t units = (steps + span_steps - 1) / span_steps;
     int64_t blocks = std::min<int64_t>((units + kWarps - 1) / kWarps, max_blocks);
     if (blocks < 1) blocks = 1;
     k<<<(unsigned)blocks, kThreads, smem, stream>>>(d, op, nchunks, span_steps * kStep);

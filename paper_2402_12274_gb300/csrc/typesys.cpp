@@ -77,6 +77,7 @@ NP make_run(int64_t len, int64_t base)
     n->tlo = base;
     n->thi = add_ck(base, len);
     n->align = std::min(p2(len), p2(base));
+    n->maxrun = len;
     n->nonoverlap = true;
     return n;
 }
@@ -122,6 +123,7 @@ NP make_reg(int64_t count, int64_t stride, const NP &child)
     n->tlo = add_ck(std::min<int64_t>(0, span), C.tlo);
     n->thi = add_ck(std::max<int64_t>(0, span), C.thi);
     n->align = std::min(C.align, p2(stride));
+    n->maxrun = C.maxrun;
     n->nonoverlap = C.nonoverlap && abs_ck(stride) >= sub_ck(C.thi, C.tlo);
     return n;
 }
@@ -229,6 +231,7 @@ NP make_list(std::vector<Entry> &&in)
             lo = std::min(lo, st[b]);
             hi = std::max(hi, add_ck(st[b], ln[b]));
             al = std::min(al, std::min(p2(st[b]), p2(ln[b])));
+            nd->maxrun = std::max(nd->maxrun, ln[b]);
             sp[b] = {st[b], st[b] + ln[b]};
         }
         nd->size = L->pbytes[r];
@@ -349,6 +352,7 @@ NP make_list(std::vector<Entry> &&in)
         const Node &K = *e.kid;
         nov = nov && K.nonoverlap &&
               (e.cnt == 1 || abs_ck(e.stride) >= sub_ck(K.thi, K.tlo) || ea[b].single);
+        nd->maxrun = std::max(nd->maxrun, ea[b].single ? ea[b].size : K.maxrun);
         sp[b] = {ea[b].tlo, ea[b].thi};
     }
     nd->tlo = lo;
@@ -512,6 +516,7 @@ std::shared_ptr<Committed> commit_node(const NP &root)
         dn[i] = d;
     }
     C->align = root->align;
+    C->maxrun = root->maxrun;
     C->nseg = root->nseg;
     C->size = root->size;
     C->nonoverlap = root->nonoverlap;
