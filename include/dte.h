@@ -314,7 +314,7 @@ DTE_API int dte_unpack_batch_enqueue(int64_t nops, const dte_op *ops, dte_stream
  * cannot wait on the allocator, libraries handed a stream but not allowed to
  * touch the device heap.  Same result as dte_pack_batch_enqueue.
  *
- * The op table goes into one fixed array of about 35 KB inside the library
+ * The op table goes into one fixed array of about 43 KB inside the library
  * (held on every GPU that loads the library until the process exits)
  * instead of memory from cudaMalloc.  Limits and rules:
  *   - nops <= DTE_NOALLOC_MAX_OPS, else DTE_ERR_UNSUPPORTED (nothing queued);
@@ -332,6 +332,57 @@ DTE_API int dte_unpack_batch_enqueue(int64_t nops, const dte_op *ops, dte_stream
  *     completion events are recorded, as creating them could allocate).
  * Returns as soon as the work is queued on `stream`. */
 DTE_API int dte_pack_batch_enqueue_noalloc(int64_t nops, const dte_op *ops, dte_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Request loop: a device-resident stand-in for the progress engine (§7
+ * general progress, §2 polled generalized requests, §5 work executed in the
+ * GPU's own context).  One persistent kernel keeps taking pack/unpack
+ * requests as the host admits them, so requests of mixed sizes that arrive
+ * while others are running are batched continuously instead of launched one
+ * by one.  Admission is first-come first-served under a byte cap and a ring
+ * of device slots.  Requests run without stream ordering: their inputs must
+ * be ready (e.g. the producing stream synchronised) when submitted, and
+ * their buffers and types must stay valid until they complete.  The loop
+ * leaves after `idle_exit_us` without work and is relaunched by the next
+ * submit/progress call; every device wait is bounded.
+ * ------------------------------------------------------------------------ */
+typedef struct dte_server_s *dte_server;
+
+typedef struct dte_server_config {
+    int64_t ring_slots;          /* requests admitted at once; power of two <= 2^20 (default 1024) */
+    int64_t max_inflight_bytes;  /* cap on moved bytes (2*count*size) of admitted, unfinished
+                                    requests (default 8 GiB); a larger request is admitted alone */
+    int32_t ctas_per_sm;         /* persistent CTAs per SM, 1 or 2 (default 2) */
+    int32_t span_tiles;          /* 2 KiB tiles (or 32-segment rounds) a warp claims at once (4) */
+    int64_t idle_exit_us;        /* empty-poll budget before the loop leaves (default 50000) */
+} dte_server_config;
+
+/* Create a request loop on the current device (cfg NULL = defaults).  Allocates
+ * the ring and control words in pinned host memory, a small device state,
+ * and its own non-blocking stream.  DTE_ERR_ARG for invalid settings. */
+DTE_API int dte_server_create(const dte_server_config *cfg, dte_server *out);
+
+/* Queue one request (kind DTE_BATCH_PACK or DTE_BATCH_UNPACK, one dte_op) and
+ * return its ticket (tickets count up from 0 in submission order).  Admits it
+ * at once if capacity allows, else keeps it queued on the host.  Never
+ * blocks.  Unpack requests into an overlapping layout: DTE_ERR_OVERLAP. */
+DTE_API int dte_server_submit(dte_server s, int kind, const dte_op *op, int64_t *ticket);
+
+/* Account completions, admit queued requests, relaunch the loop if needed;
+ * report requests on the device (*inflight) and queued on the host (*queued).
+ * Either pointer may be NULL. */
+DTE_API int dte_server_progress(dte_server s, int64_t *inflight, int64_t *queued);
+
+/* *done = 1 if the ticket's request has completed (its bytes are in place). */
+DTE_API int dte_server_test(dte_server s, int64_t ticket, int *done);
+
+/* Drive progress until the ticket completes or timeout_us elapses
+ * (DTE_ERR_TIMEOUT). */
+DTE_API int dte_server_wait(dte_server s, int64_t ticket, int64_t timeout_us);
+
+/* Stop the loop (it leaves at its next poll), wait for it, release
+ * everything and set *s = NULL.  Requests not yet completed are abandoned. */
+DTE_API int dte_server_free(dte_server *s);
 
 #ifdef __cplusplus
 }

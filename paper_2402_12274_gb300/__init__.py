@@ -56,6 +56,11 @@ class dte_op(C.Structure):
 BATCH_UNPACK, BATCH_PACK = 0, 1
 
 
+class dte_server_config(C.Structure):
+    _fields_ = [("ring_slots", C.c_int64), ("max_inflight_bytes", C.c_int64), ("ctas_per_sm", C.c_int32),
+                ("span_tiles", C.c_int32), ("idle_exit_us", C.c_int64)]
+
+
 # error codes (include/dte.h)
 SUCCESS, ERR_ARG, ERR_TYPE, ERR_OVERFLOW, ERR_TRUNCATE, ERR_OVERLAP, ERR_NOMEM, ERR_CUDA, \
     ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_NODEVICE = range(11)
@@ -105,6 +110,12 @@ _SIGS = {
     "dte_unpack_batch_enqueue": ([_i64, C.POINTER(dte_op), _p], C.c_int),
     "dte_pack_batch_enqueue_noalloc": ([_i64, C.POINTER(dte_op), _p], C.c_int),
     "dte_pack_adjoint_f32_enqueue": ([_p, _i64, _p, _p, _p], C.c_int),
+    "dte_server_create": ([C.POINTER(dte_server_config), _pp], C.c_int),
+    "dte_server_submit": ([_p, C.c_int, C.POINTER(dte_op), _pi64], C.c_int),
+    "dte_server_progress": ([_p, _pi64, _pi64], C.c_int),
+    "dte_server_test": ([_p, _i64, C.POINTER(C.c_int)], C.c_int),
+    "dte_server_wait": ([_p, _i64, _i64], C.c_int),
+    "dte_server_free": ([_pp], C.c_int),
 }
 NOALLOC_MAX_OPS = 256  # DTE_NOALLOC_MAX_OPS in include/dte.h
 for _n, (_a, _r) in _SIGS.items():
@@ -364,6 +375,42 @@ def dte_unpack_batch_enqueue(ops, stream: int = 0):
 def dte_pack_adjoint_f32_enqueue(gy: int, count: int, t: int, gx: int, stream: int = 0):
     """gx[src(k)] += gy[k] for the float32 pack of `count` elements of t."""
     _ck(lib.dte_pack_adjoint_f32_enqueue(gy, count, t, gx, stream), "dte_pack_adjoint_f32_enqueue")
+
+
+def dte_server_create(ring_slots: int = 1024, max_inflight_bytes: int = 8 << 30, ctas_per_sm: int = 2,
+                      span_tiles: int = 4, idle_exit_us: int = 50000) -> int:
+    cfg = dte_server_config(ring_slots, max_inflight_bytes, ctas_per_sm, span_tiles, idle_exit_us)
+    out = C.c_void_p()
+    _ck(lib.dte_server_create(C.byref(cfg), C.byref(out)), "dte_server_create")
+    return out.value
+
+
+def dte_server_submit(server: int, kind: int, t: int, count: int, user: int, packed: int) -> int:
+    op = dte_op(t, count, user, packed)
+    ticket = C.c_int64()
+    _ck(lib.dte_server_submit(server, kind, C.byref(op), C.byref(ticket)), "dte_server_submit")
+    return ticket.value
+
+
+def dte_server_progress(server: int):
+    a, b = C.c_int64(), C.c_int64()
+    _ck(lib.dte_server_progress(server, C.byref(a), C.byref(b)), "dte_server_progress")
+    return a.value, b.value
+
+
+def dte_server_test(server: int, ticket: int) -> bool:
+    d = C.c_int()
+    _ck(lib.dte_server_test(server, ticket, C.byref(d)), "dte_server_test")
+    return bool(d.value)
+
+
+def dte_server_wait(server: int, ticket: int, timeout_us: int = 10_000_000):
+    _ck(lib.dte_server_wait(server, ticket, timeout_us), "dte_server_wait")
+
+
+def dte_server_free(server: int):
+    h = C.c_void_p(server)
+    _ck(lib.dte_server_free(C.byref(h)), "dte_server_free")
 
 
 def dte_pack_batch_enqueue_noalloc(ops, stream: int = 0):

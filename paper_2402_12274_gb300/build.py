@@ -17,8 +17,8 @@ ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libdte.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
 
-SOURCES = ["typesys.cpp", "kernels.cu"]
-HEADERS = ["desc.h", "internal.h"]
+SOURCES = ["typesys.cpp", "kernels.cu", "server.cu"]
+HEADERS = ["desc.h", "internal.h", "move.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2,-fvisibility=hidden",
           "-I", os.path.join(ROOT, "include")]

@@ -36,253 +36,9 @@
 #include <vector>
 
 #include "internal.h"
+#include "move.cuh"
 
 namespace dte {
-
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
-#ifndef DTE_KU
-#define DTE_KU 4
-#endif
-constexpr int kU = DTE_KU;            // chunks per lane per step
-constexpr int kStep = 32 * kU;        // chunks per warp step (2 KiB)
-#ifndef DTE_MINBLOCKS
-#define DTE_MINBLOCKS 4
-#endif
-constexpr int kMinBlocks = DTE_MINBLOCKS;  // CTAs per SM the data kernels are sized for (<= 64 regs)
-constexpr int64_t kSmemBlob = 16384;  // stage descriptors up to this size whole
-constexpr int64_t kSegMaxRun = 256;   // segment-major kernel for runs up to this length
-constexpr int kMaxSmemNodes = 64;
-
-enum : int { STAGE_NONE = 0, STAGE_NODES = 1, STAGE_BLOB = 2 };
-
-// What a kernel needs to walk one committed type.
-struct Desc {
-    const char *blob;
-    int64_t blob_bytes;
-    int32_t root;
-    int32_t nnodes;
-    int32_t stage;
-    int32_t pad_;
-};
-
-// One data movement: element e of the user layout starts at user + e*extent.
-struct Op {
-    const char *user_in;    // pack source
-    char *user_out;         // unpack destination
-    const char *packed_in;  // unpack source (position applied)
-    char *packed_out;       // pack destination (position applied)
-    int64_t total;          // bytes moved
-    int64_t esize;          // element size
-    int64_t extent;         // element stride
-    FastDiv ediv;           // / esize
-    int32_t root;
-    int32_t pad_;
-};
-
-__device__ __forceinline__ void stage_desc(const Desc &d, uint4 *smem, const char *&blob,
-                                           const DNode *&nodes)
-{
-    const DNode *g = reinterpret_cast<const DNode *>(d.blob + sizeof(BlobHeader));
-    if (d.stage == STAGE_BLOB) {
-        const uint4 *s = reinterpret_cast<const uint4 *>(d.blob);
-        int nw = (int)(d.blob_bytes / 16);
-        for (int i = threadIdx.x; i < nw; i += blockDim.x) smem[i] = s[i];
-        __syncthreads();
-        blob = reinterpret_cast<const char *>(smem);
-        nodes = reinterpret_cast<const DNode *>(blob + sizeof(BlobHeader));
-    } else if (d.stage == STAGE_NODES) {
-        const uint4 *s = reinterpret_cast<const uint4 *>(g);
-        int nw = d.nnodes * (int)(sizeof(DNode) / 16);
-        for (int i = threadIdx.x; i < nw; i += blockDim.x) smem[i] = s[i];
-        __syncthreads();
-        blob = d.blob;
-        nodes = reinterpret_cast<const DNode *>(smem);
-    } else {
-        blob = d.blob;
-        nodes = g;
-    }
-}
-
-template <int W> struct Word;
-template <> struct Word<1> { using T = uint8_t; };
-template <> struct Word<2> { using T = uint16_t; };
-template <> struct Word<4> { using T = uint32_t; };
-template <> struct Word<8> { using T = unsigned long long; };
-template <> struct Word<16> { using T = uint4; };
-
-template <int W>
-union Chunk {
-    uint4 v;
-    typename Word<W>::T w[16 / W];
-};
-
-// packed offset P -> user displacement and bytes left in that run
-__device__ __forceinline__ void locate(const Op &op, const DNode *nodes, const char *blob, int64_t P,
-                                       int64_t &d, int64_t &rem, Hint &h)
-{
-    int64_t e = fdiv(P, op.ediv);
-    d = e * op.extent;
-    decode_bytes(nodes, blob, op.root, P - e * op.esize, d, rem, h);
-}
-
-template <int W>
-__device__ __forceinline__ typename Word<W>::T ldw(const char *p)
-{
-    return __ldg(reinterpret_cast<const typename Word<W>::T *>(p));
-}
-
-template <int W>
-__device__ __forceinline__ void stw(char *p, typename Word<W>::T v)
-{
-    *reinterpret_cast<typename Word<W>::T *>(p) = v;
-}
-
-// gather the nb (<= 16) packed bytes starting at P from the user layout
-template <int W>
-__device__ __forceinline__ uint4 gather_chunk(const Op &op, const DNode *nodes, const char *blob, int64_t P,
-                                              int nb, Hint &h)
-{
-    Chunk<W> c;
-    if (W == 16) {
-        int64_t d, rem;
-        locate(op, nodes, blob, P, d, rem, h);
-        c.v = ldw<16>(op.user_in + d);
-        return c.v;
-    }
-    c.v = make_uint4(0, 0, 0, 0);
-    int64_t d = 0, rem = 0;
-#pragma unroll
-    for (int s = 0; s < 16 / W; s++) {
-        if (s * W < nb) {
-            if (rem <= 0) locate(op, nodes, blob, P + s * W, d, rem, h);
-            c.w[s] = ldw<W>(op.user_in + d);
-            d += W;
-            rem -= W;
-        }
-    }
-    return c.v;
-}
-
-template <int W>
-__device__ __forceinline__ void scatter_chunk(const Op &op, const DNode *nodes, const char *blob, int64_t P,
-                                              int nb, uint4 v, Hint &h)
-{
-    Chunk<W> c;
-    c.v = v;
-    if (W == 16) {
-        int64_t d, rem;
-        locate(op, nodes, blob, P, d, rem, h);
-        *reinterpret_cast<uint4 *>(op.user_out + d) = c.v;
-        return;
-    }
-    int64_t d = 0, rem = 0;
-#pragma unroll
-    for (int s = 0; s < 16 / W; s++) {
-        if (s * W < nb) {
-            if (rem <= 0) locate(op, nodes, blob, P + s * W, d, rem, h);
-            stw<W>(op.user_out + d, c.w[s]);
-            d += W;
-            rem -= W;
-        }
-    }
-}
-
-template <int W, bool PK16>
-__device__ __forceinline__ uint4 load_packed(const char *p, int nb)
-{
-    if (W == 16 || (PK16 && nb == 16)) return __ldg(reinterpret_cast<const uint4 *>(p));
-    Chunk<W> c;
-    c.v = make_uint4(0, 0, 0, 0);
-#pragma unroll
-    for (int s = 0; s < 16 / W; s++)
-        if (s * W < nb) c.w[s] = ldw<W>(p + s * W);
-    return c.v;
-}
-
-template <int W, bool PK16>
-__device__ __forceinline__ void store_packed(char *p, uint4 v, int nb)
-{
-    if (W == 16 || (PK16 && nb == 16)) {
-        *reinterpret_cast<uint4 *>(p) = v;
-        return;
-    }
-    Chunk<W> c;
-    c.v = v;
-#pragma unroll
-    for (int s = 0; s < 16 / W; s++)
-        if (s * W < nb) stw<W>(p + s * W, c.w[s]);
-}
-
-// One warp step, 16-byte words: a lane's chunks sit 512 bytes apart, so when
-// the run found for its first chunk extends past a later chunk, that chunk's
-// user address follows without walking the descriptor again.
-template <bool PACK>
-__device__ __forceinline__ void warp_step16(const Op &op, const DNode *nodes, const char *blob, int64_t base,
-                                            int64_t end, int lane, Hint *h)
-{
-    uint4 v[kU];
-    int64_t d[kU];
-    int64_t d0 = 0, rem0 = 0;
-#pragma unroll
-    for (int u = 0; u < kU; u++) {
-        int64_t c = base + u * 32 + lane;
-        if (c < end) {
-            if (u > 0 && rem0 >= (int64_t)u * 512 + 16) {
-                d[u] = d0 + u * 512;
-            } else {
-                int64_t rem;
-                locate(op, nodes, blob, c * 16, d[u], rem, h[u]);
-                if (u == 0) {
-                    d0 = d[u];
-                    rem0 = rem;
-                }
-            }
-            if (PACK) v[u] = __ldg(reinterpret_cast<const uint4 *>(op.user_in + d[u]));
-            else v[u] = __ldg(reinterpret_cast<const uint4 *>(op.packed_in + c * 16));
-        }
-    }
-#pragma unroll
-    for (int u = 0; u < kU; u++) {
-        int64_t c = base + u * 32 + lane;
-        if (c < end) {
-            if (PACK) *reinterpret_cast<uint4 *>(op.packed_out + c * 16) = v[u];
-            else *reinterpret_cast<uint4 *>(op.user_out + d[u]) = v[u];
-        }
-    }
-}
-
-// One warp step: chunks [base, base + kStep) clipped to `end`.
-template <int W, bool PACK, bool PK16>
-__device__ __forceinline__ void warp_step(const Op &op, const DNode *nodes, const char *blob, int64_t base,
-                                          int64_t end, int lane, Hint *h)
-{
-    if (W == 16) {
-        warp_step16<PACK>(op, nodes, blob, base, end, lane, h);
-        return;
-    }
-    uint4 v[kU];
-#pragma unroll
-    for (int u = 0; u < kU; u++) {
-        int64_t c = base + u * 32 + lane;
-        if (c < end) {
-            int64_t P = c * 16;
-            int nb = (int)(op.total - P < 16 ? op.total - P : 16);
-            if (PACK) v[u] = gather_chunk<W>(op, nodes, blob, P, nb, h[u]);
-            else v[u] = load_packed<W, PK16>(op.packed_in + P, nb);
-        }
-    }
-#pragma unroll
-    for (int u = 0; u < kU; u++) {
-        int64_t c = base + u * 32 + lane;
-        if (c < end) {
-            int64_t P = c * 16;
-            int nb = (int)(op.total - P < 16 ? op.total - P : 16);
-            if (PACK) store_packed<W, PK16>(op.packed_out + P, v[u], nb);
-            else scatter_chunk<W>(op, nodes, blob, P, nb, v[u], h[u]);
-        }
-    }
-}
 
 // Warps take spans of `span` chunks (a multiple of kStep) round-robin, so
 // every warp sees every part of the layout (costly and cheap regions mix)
@@ -322,77 +78,20 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) seg_kernel(Desc d, Op op
     const char *blob;
     const DNode *nodes;
     stage_desc(d, smem, blob, nodes);
-    using T = typename Word<W>::T;
-    const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int64_t stride = (int64_t)gridDim.x * kWarps * span;
     Hint h{-1, 0};
     for (int64_t s0 = warp * span; s0 < nsegs; s0 += stride) {
         const int64_t s1 = min(s0 + span, nsegs);
-        for (int64_t base = s0; base < s1; base += 32) {
-            const int nvalid = (int)min((int64_t)32, s1 - base);
-            int64_t disp = 0, len = 0, ps = 0;
-            if (lane < nvalid) {
-                const int64_t k = base + lane;
-                const int64_t e = fdiv(k, div_nseg);
-                disp = e * op.extent;
-                decode_seg(nodes, blob, op.root, k - e * nseg_elem, disp, len, ps, h);
-                ps += e * op.esize;
-            }
-            const int64_t p0 = __shfl_sync(FULL, ps, 0);
-            const int64_t p1 = __shfl_sync(FULL, ps + len, nvalid - 1);
-            const int64_t nwords = (p1 - p0) / W;
-            for (int64_t w0 = 0; w0 < nwords; w0 += 32 * kU) {
-                T v[kU];
-                int64_t ud[kU];
-#pragma unroll
-                for (int u = 0; u < kU; u++) {
-                    const int64_t wi = w0 + u * 32 + lane;
-                    const int64_t q = p0 + wi * W;
-                    int lo = 0;
-#pragma unroll
-                    for (int step = 16; step >= 1; step >>= 1) {
-                        const int cand = lo + step;
-                        const int64_t pc = __shfl_sync(FULL, ps, cand & 31);
-                        if (cand < nvalid && pc <= q) lo = cand;
-                    }
-                    ud[u] = __shfl_sync(FULL, disp, lo) + (q - __shfl_sync(FULL, ps, lo));
-                    if (wi < nwords) {
-                        if (PACK) v[u] = ldw<W>(op.user_in + ud[u]);
-                        else v[u] = ldw<W>(op.packed_in + q);
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < kU; u++) {
-                    const int64_t wi = w0 + u * 32 + lane;
-                    if (wi < nwords) {
-                        if (PACK) stw<W>(op.packed_out + p0 + wi * W, v[u]);
-                        else stw<W>(op.user_out + ud[u], v[u]);
-                    }
-                }
-            }
-        }
+        for (int64_t base = s0; base < s1; base += 32)
+            seg_round<W, PACK>(op, nodes, blob, nseg_elem, div_nseg, base, s1, lane, h);
     }
 }
 
 // ---------------------------------------------------------------------------
 // batched movement: one persistent launch over many independent operations
 // ---------------------------------------------------------------------------
-struct BatchOp {
-    Desc d;
-    Op op;
-    int64_t nchunks;
-    int32_t wsel;   // word-size variant (see wsel_of)
-    int32_t soff;   // offset of the descriptor in the group's staged image, or -1
-};
-
-__host__ __device__ constexpr int wsel_of(int W, bool pk16)
-{
-    return W == 16 ? 0 : W == 8 ? (pk16 ? 1 : 2) : W == 4 ? (pk16 ? 3 : 4) : W == 2 ? (pk16 ? 5 : 6)
-                                                                                 : (pk16 ? 7 : 8);
-}
-
 // One launch per copy-word class present in a batch: ops are grouped by
 // (W, packed side 16-aligned) so each kernel is specialised like move_kernel.
 // tile0: nops+1 prefix of 2 KiB tiles per op of the group.  Warps take spans
@@ -436,12 +135,54 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_kernel(const Batch
     }
 }
 
+// Segment-major batch variant: a tile of a segment-major op is one round of
+// 32 segments.
+template <int W, bool PACK>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) batch_seg_kernel(const BatchOp *ops, const int64_t *tile0,
+                                                                        int64_t nops, int64_t ntiles, int64_t span,
+                                                                        const char *image, int64_t image_bytes)
+{
+    extern __shared__ uint4 smem[];
+    if (image_bytes > 0) {
+        const uint4 *s = reinterpret_cast<const uint4 *>(image);
+        int nw = (int)(image_bytes / 16);
+        for (int i = threadIdx.x; i < nw; i += blockDim.x) smem[i] = s[i];
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int64_t stride = (int64_t)gridDim.x * kWarps * span;
+    Hint oh{-1, 0};
+    Hint h{-1, 0};
+    int64_t cur = -1;
+    for (int64_t s0 = warp * span; s0 < ntiles; s0 += stride) {
+        const int64_t s1 = min(s0 + span, ntiles);
+        for (int64_t t = s0; t < s1; t++) {
+            int64_t i = find_le(tile0, nops, t, oh, 0);
+            if (i != cur) {
+                h = Hint{-1, 0};
+                cur = i;
+            }
+            const BatchOp *b = ops + i;
+            const int soff = b->soff;
+            const char *blob = soff >= 0 ? reinterpret_cast<const char *>(smem) + soff : b->d.blob;
+            const DNode *nodes = reinterpret_cast<const DNode *>(blob + sizeof(BlobHeader));
+            const int64_t base = (t - tile0[i]) * 32;
+            seg_round<W, PACK>(b->op, nodes, blob, b->nseg_elem, b->div_nseg, base, b->nsegs, lane, h);
+        }
+    }
+}
+
 typedef void (*BatchKernel)(const BatchOp *, const int64_t *, int64_t, int64_t, int64_t, const char *, int64_t);
 
 template <bool PACK>
 static BatchKernel pick_batch(int wsel)
 {
     switch (wsel) {
+    case 9: return batch_seg_kernel<8, PACK>;
+    case 10: return batch_seg_kernel<4, PACK>;
+    case 11: return batch_seg_kernel<2, PACK>;
+    case 12: return batch_seg_kernel<1, PACK>;
     case 0: return batch_kernel<16, PACK, true>;
     case 1: return batch_kernel<8, PACK, true>;
     case 2: return batch_kernel<8, PACK, false>;
@@ -643,91 +384,6 @@ __global__ void __launch_bounds__(kThreads) adjoint_csr_kernel(const int64_t *ro
 // ---------------------------------------------------------------------------
 // launch helpers
 // ---------------------------------------------------------------------------
-static int sm_count(int dev)
-{
-    static int cache[64];
-    int &c = cache[dev & 63];
-    if (c == 0) {
-        int v = 0;
-        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-        c = v > 0 ? v : 1;
-    }
-    return c;
-}
-
-template <typename K>
-static int occupancy(K kernel, size_t smem)
-{
-    int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, kThreads, smem) != cudaSuccess ||
-        blocks <= 0) {
-        cudaGetLastError();
-        blocks = 1;
-    }
-    return blocks;
-}
-
-static Desc make_desc(const Committed &c, const char *dblob, size_t *smem)
-{
-    Desc d;
-    d.blob = dblob;
-    d.blob_bytes = c.bytes;
-    d.root = c.root;
-    d.nnodes = c.nnodes;
-    d.pad_ = 0;
-    if (c.bytes <= kSmemBlob) {
-        d.stage = STAGE_BLOB;
-        *smem = (size_t)c.bytes;
-    } else if (c.nnodes <= kMaxSmemNodes) {
-        d.stage = STAGE_NODES;
-        *smem = (size_t)c.nnodes * sizeof(DNode);
-    } else {
-        d.stage = STAGE_NONE;
-        *smem = 0;
-    }
-    return d;
-}
-
-static int64_t p2addr(const void *p)
-{
-    uintptr_t u = (uintptr_t)p;
-    if (u == 0) return 16;
-    uintptr_t low = u & (~u + 1);
-    return low >= 16 ? 16 : (int64_t)low;
-}
-
-static int64_t p2v(int64_t v)
-{
-    if (v == 0) return 16;
-    uint64_t u = (uint64_t)v;
-    uint64_t low = u & (~u + 1);
-    return low >= 16 ? 16 : (int64_t)low;
-}
-
-// copy word for one operation
-static int word_of(const Committed &c, int64_t extent, int64_t count, const void *user, const void *packed)
-{
-    int64_t W = std::min<int64_t>(c.align, std::min(p2addr(user), p2addr(packed)));
-    if (count > 1) W = std::min(W, p2v(extent));
-    return (int)W;
-}
-
-static Op make_op(const Committed &c, int64_t extent, const void *user, void *packed, int64_t count)
-{
-    Op op;
-    op.user_in = (const char *)user;
-    op.user_out = (char *)user;
-    op.packed_in = (const char *)packed;
-    op.packed_out = (char *)packed;
-    op.total = count * c.size;
-    op.esize = c.size;
-    op.extent = extent;
-    op.ediv = c.nodes()[c.root].div_size;
-    op.root = c.root;
-    op.pad_ = 0;
-    return op;
-}
-
 typedef void (*MoveKernel)(Desc, Op, int64_t, int64_t);
 
 template <bool PACK>
@@ -796,26 +452,6 @@ static int launch_move(bool pack, dte_type t, const char *dblob, const void *use
     k<<<(unsigned)blocks, kThreads, smem, stream>>>(d, op, nchunks, span_steps * kStep);
     if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
     return DTE_SUCCESS;
-}
-
-static bool capturing(dte_stream_t stream)
-{
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return cs != cudaStreamCaptureStatusNone;
-}
-
-// Resolve the device descriptor; frees finished deferred descriptors unless
-// the stream is being captured (no event polling inside a capture).
-static int prep(dte_type t, dte_stream_t stream, const char **blob, int *dev)
-{
-    if (!handle_valid(t)) return DTE_ERR_TYPE;
-    if (!t->committed) return DTE_ERR_TYPE;
-    if (!capturing(stream)) reap_deferred();
-    return device_blob(t, blob, dev);
 }
 
 }  // namespace dte
@@ -1003,13 +639,7 @@ int dte_batch_create(int kind, int64_t nops, const dte_op *ops, dte_batch *out)
                 if ((rc = device_blob(o.type, &dblob, &d2)) != DTE_SUCCESS) break;
                 Committed &c = *o.type->desc;
                 hc[(size_t)i] = &c;
-                size_t smem;
-                h.d = make_desc(c, dblob, &smem);
-                h.soff = -1;
-                h.op = make_op(c, o.type->extent(), o.user, o.packed, o.count);
-                h.nchunks = (total + 15) / 16;
-                int W = word_of(c, o.type->extent(), o.count, o.user, o.packed);
-                h.wsel = wsel_of(W, p2addr(o.packed) >= 16);
+                fill_batch_op(h, c, o.type->extent(), o, dblob);
                 b->keep.push_back(o.type->desc);
             }
         }
@@ -1017,13 +647,13 @@ int dte_batch_create(int kind, int64_t nops, const dte_op *ops, dte_batch *out)
             delete b;
             return rc;
         }
-        // group the non-empty ops by copy-word class, keeping their order
+        // group the non-empty ops by kernel variant, keeping their order
         std::vector<BatchOp> grouped;
         std::vector<const Committed *> gc;
         std::vector<int64_t> prefix;
         std::vector<char> image;  // staged descriptor images of all groups
         grouped.reserve((size_t)nops);
-        for (int w = 0; w < 9; w++) {
+        for (int w = 0; w < kNumClasses; w++) {
             BatchGroup g{w, (int64_t)grouped.size(), 0, (int64_t)prefix.size(), 0, 0, 0, 0};
             prefix.push_back(0);
             for (size_t i = 0; i < hops.size(); i++) {
@@ -1031,7 +661,7 @@ int dte_batch_create(int kind, int64_t nops, const dte_op *ops, dte_batch *out)
                 if (h.nchunks == 0 || h.wsel != w) continue;
                 grouped.push_back(h);
                 gc.push_back(hc[i]);
-                prefix.push_back(prefix.back() + (h.nchunks + kStep - 1) / kStep);
+                prefix.push_back(prefix.back() + op_tiles(h));
             }
             g.nops = (int64_t)grouped.size() - g.op0;
             if (g.nops == 0) {
@@ -1324,7 +954,7 @@ constexpr int64_t kNoAllocMaxOps = DTE_NOALLOC_MAX_OPS;
 
 struct NoAllocTable {
     BatchOp ops[kNoAllocMaxOps];
-    int64_t prefix[kNoAllocMaxOps + 9];  // per-group tile prefixes (<= 9 groups)
+    int64_t prefix[kNoAllocMaxOps + kNumClasses];  // per-group tile prefixes
 };
 
 static __device__ __align__(256) char g_noalloc_scratch[sizeof(NoAllocTable)];
@@ -1379,26 +1009,20 @@ extern "C" int dte_pack_batch_enqueue_noalloc(int64_t nops, const dte_op *ops, d
             const char *dblob;
             // the descriptor must already be on this device (commit uploads it)
             if (int rc = device_blob_resident(o.type, dev, &dblob)) return rc;
-            Committed &c = *o.type->desc;
-            size_t smem;
-            h.d = make_desc(c, dblob, &smem);
-            h.soff = -1;
-            h.op = make_op(c, o.type->extent(), o.user, o.packed, o.count);
-            h.nchunks = (total + 15) / 16;
-            h.wsel = wsel_of(word_of(c, o.type->extent(), o.count, o.user, o.packed), p2addr(o.packed) >= 16);
+            fill_batch_op(h, *o.type->desc, o.type->extent(), o, dblob);
         }
-        // group by copy-word class exactly like the allocating batch
+        // group by kernel variant exactly like the allocating batch
         struct G { int wsel; int64_t op0, nops, t0, ntiles; };
-        G groups[9];
+        G groups[kNumClasses];
         int ng = 0;
         int64_t n = 0, np = 0;
-        for (int w = 0; w < 9; w++) {
+        for (int w = 0; w < kNumClasses; w++) {
             G g{w, n, 0, np, 0};
             table.prefix[np++] = 0;
             for (int64_t i = 0; i < nops; i++) {
                 if (staged[i].nchunks == 0 || staged[i].wsel != w) continue;
                 table.ops[n++] = staged[i];
-                table.prefix[np] = table.prefix[np - 1] + (staged[i].nchunks + kStep - 1) / kStep;
+                table.prefix[np] = table.prefix[np - 1] + op_tiles(staged[i]);
                 np++;
             }
             g.nops = n - g.op0;
@@ -1421,7 +1045,7 @@ extern "C" int dte_pack_batch_enqueue_noalloc(int64_t nops, const dte_op *ops, d
             cudaGetLastError();
             return DTE_ERR_CUDA;
         }
-        static thread_local int occ_cache[64][9];
+        static thread_local int occ_cache[64][kNumClasses];
         for (int gi = 0; gi < ng; gi++) {
             const G &g = groups[gi];
             BatchKernel k = pick_batch<true>(g.wsel);

@@ -1,0 +1,480 @@
+// move.cuh -- building blocks shared by the data-movement kernels (single
+// operations, batches, the request loop): launch constants, the records a
+// kernel needs for one operation, the warp-level chunk and segment steps,
+// and the host helpers that choose a kernel variant for an operation.
+// See kernels.cu for the design of the two work splits (chunk-major and
+// segment-major).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "internal.h"
+
+namespace dte {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+#ifndef DTE_KU
+#define DTE_KU 4
+#endif
+constexpr int kU = DTE_KU;            // chunks per lane per step
+constexpr int kStep = 32 * kU;        // chunks per warp step (2 KiB)
+#ifndef DTE_MINBLOCKS
+#define DTE_MINBLOCKS 4
+#endif
+constexpr int kMinBlocks = DTE_MINBLOCKS;  // CTAs per SM the data kernels are sized for (<= 64 regs)
+constexpr int64_t kSmemBlob = 16384;  // stage descriptors up to this size whole
+constexpr int64_t kSegMaxRun = 256;   // segment-major kernel for runs up to this length
+constexpr int kMaxSmemNodes = 64;
+
+enum : int { STAGE_NONE = 0, STAGE_NODES = 1, STAGE_BLOB = 2 };
+
+// What a kernel needs to walk one committed type.
+struct Desc {
+    const char *blob;
+    int64_t blob_bytes;
+    int32_t root;
+    int32_t nnodes;
+    int32_t stage;
+    int32_t pad_;
+};
+
+// One data movement: element e of the user layout starts at user + e*extent.
+struct Op {
+    const char *user_in;    // pack source
+    char *user_out;         // unpack destination
+    const char *packed_in;  // unpack source (position applied)
+    char *packed_out;       // pack destination (position applied)
+    int64_t total;          // bytes moved
+    int64_t esize;          // element size
+    int64_t extent;         // element stride
+    FastDiv ediv;           // / esize
+    int32_t root;
+    int32_t pad_;
+};
+
+__device__ __forceinline__ void stage_desc(const Desc &d, uint4 *smem, const char *&blob,
+                                           const DNode *&nodes)
+{
+    const DNode *g = reinterpret_cast<const DNode *>(d.blob + sizeof(BlobHeader));
+    if (d.stage == STAGE_BLOB) {
+        const uint4 *s = reinterpret_cast<const uint4 *>(d.blob);
+        int nw = (int)(d.blob_bytes / 16);
+        for (int i = threadIdx.x; i < nw; i += blockDim.x) smem[i] = s[i];
+        __syncthreads();
+        blob = reinterpret_cast<const char *>(smem);
+        nodes = reinterpret_cast<const DNode *>(blob + sizeof(BlobHeader));
+    } else if (d.stage == STAGE_NODES) {
+        const uint4 *s = reinterpret_cast<const uint4 *>(g);
+        int nw = d.nnodes * (int)(sizeof(DNode) / 16);
+        for (int i = threadIdx.x; i < nw; i += blockDim.x) smem[i] = s[i];
+        __syncthreads();
+        blob = d.blob;
+        nodes = reinterpret_cast<const DNode *>(smem);
+    } else {
+        blob = d.blob;
+        nodes = g;
+    }
+}
+
+template <int W> struct Word;
+template <> struct Word<1> { using T = uint8_t; };
+template <> struct Word<2> { using T = uint16_t; };
+template <> struct Word<4> { using T = uint32_t; };
+template <> struct Word<8> { using T = unsigned long long; };
+template <> struct Word<16> { using T = uint4; };
+
+template <int W>
+union Chunk {
+    uint4 v;
+    typename Word<W>::T w[16 / W];
+};
+
+// packed offset P -> user displacement and bytes left in that run
+__device__ __forceinline__ void locate(const Op &op, const DNode *nodes, const char *blob, int64_t P,
+                                       int64_t &d, int64_t &rem, Hint &h)
+{
+    int64_t e = fdiv(P, op.ediv);
+    d = e * op.extent;
+    decode_bytes(nodes, blob, op.root, P - e * op.esize, d, rem, h);
+}
+
+template <int W>
+__device__ __forceinline__ typename Word<W>::T ldw(const char *p)
+{
+    return __ldg(reinterpret_cast<const typename Word<W>::T *>(p));
+}
+
+template <int W>
+__device__ __forceinline__ void stw(char *p, typename Word<W>::T v)
+{
+    *reinterpret_cast<typename Word<W>::T *>(p) = v;
+}
+
+// gather the nb (<= 16) packed bytes starting at P from the user layout
+template <int W>
+__device__ __forceinline__ uint4 gather_chunk(const Op &op, const DNode *nodes, const char *blob, int64_t P,
+                                              int nb, Hint &h)
+{
+    Chunk<W> c;
+    if (W == 16) {
+        int64_t d, rem;
+        locate(op, nodes, blob, P, d, rem, h);
+        c.v = ldw<16>(op.user_in + d);
+        return c.v;
+    }
+    c.v = make_uint4(0, 0, 0, 0);
+    int64_t d = 0, rem = 0;
+#pragma unroll
+    for (int s = 0; s < 16 / W; s++) {
+        if (s * W < nb) {
+            if (rem <= 0) locate(op, nodes, blob, P + s * W, d, rem, h);
+            c.w[s] = ldw<W>(op.user_in + d);
+            d += W;
+            rem -= W;
+        }
+    }
+    return c.v;
+}
+
+template <int W>
+__device__ __forceinline__ void scatter_chunk(const Op &op, const DNode *nodes, const char *blob, int64_t P,
+                                              int nb, uint4 v, Hint &h)
+{
+    Chunk<W> c;
+    c.v = v;
+    if (W == 16) {
+        int64_t d, rem;
+        locate(op, nodes, blob, P, d, rem, h);
+        *reinterpret_cast<uint4 *>(op.user_out + d) = c.v;
+        return;
+    }
+    int64_t d = 0, rem = 0;
+#pragma unroll
+    for (int s = 0; s < 16 / W; s++) {
+        if (s * W < nb) {
+            if (rem <= 0) locate(op, nodes, blob, P + s * W, d, rem, h);
+            stw<W>(op.user_out + d, c.w[s]);
+            d += W;
+            rem -= W;
+        }
+    }
+}
+
+template <int W, bool PK16>
+__device__ __forceinline__ uint4 load_packed(const char *p, int nb)
+{
+    if (W == 16 || (PK16 && nb == 16)) return __ldg(reinterpret_cast<const uint4 *>(p));
+    Chunk<W> c;
+    c.v = make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int s = 0; s < 16 / W; s++)
+        if (s * W < nb) c.w[s] = ldw<W>(p + s * W);
+    return c.v;
+}
+
+template <int W, bool PK16>
+__device__ __forceinline__ void store_packed(char *p, uint4 v, int nb)
+{
+    if (W == 16 || (PK16 && nb == 16)) {
+        *reinterpret_cast<uint4 *>(p) = v;
+        return;
+    }
+    Chunk<W> c;
+    c.v = v;
+#pragma unroll
+    for (int s = 0; s < 16 / W; s++)
+        if (s * W < nb) stw<W>(p + s * W, c.w[s]);
+}
+
+// One warp step, 16-byte words: a lane's chunks sit 512 bytes apart, so when
+// the run found for its first chunk extends past a later chunk, that chunk's
+// user address follows without walking the descriptor again.
+template <bool PACK>
+__device__ __forceinline__ void warp_step16(const Op &op, const DNode *nodes, const char *blob, int64_t base,
+                                            int64_t end, int lane, Hint *h)
+{
+    uint4 v[kU];
+    int64_t d[kU];
+    int64_t d0 = 0, rem0 = 0;
+#pragma unroll
+    for (int u = 0; u < kU; u++) {
+        int64_t c = base + u * 32 + lane;
+        if (c < end) {
+            if (u > 0 && rem0 >= (int64_t)u * 512 + 16) {
+                d[u] = d0 + u * 512;
+            } else {
+                int64_t rem;
+                locate(op, nodes, blob, c * 16, d[u], rem, h[u]);
+                if (u == 0) {
+                    d0 = d[u];
+                    rem0 = rem;
+                }
+            }
+            if (PACK) v[u] = __ldg(reinterpret_cast<const uint4 *>(op.user_in + d[u]));
+            else v[u] = __ldg(reinterpret_cast<const uint4 *>(op.packed_in + c * 16));
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; u++) {
+        int64_t c = base + u * 32 + lane;
+        if (c < end) {
+            if (PACK) *reinterpret_cast<uint4 *>(op.packed_out + c * 16) = v[u];
+            else *reinterpret_cast<uint4 *>(op.user_out + d[u]) = v[u];
+        }
+    }
+}
+
+// One warp step: chunks [base, base + kStep) clipped to `end`.
+template <int W, bool PACK, bool PK16>
+__device__ __forceinline__ void warp_step(const Op &op, const DNode *nodes, const char *blob, int64_t base,
+                                          int64_t end, int lane, Hint *h)
+{
+    if (W == 16) {
+        warp_step16<PACK>(op, nodes, blob, base, end, lane, h);
+        return;
+    }
+    uint4 v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; u++) {
+        int64_t c = base + u * 32 + lane;
+        if (c < end) {
+            int64_t P = c * 16;
+            int nb = (int)(op.total - P < 16 ? op.total - P : 16);
+            if (PACK) v[u] = gather_chunk<W>(op, nodes, blob, P, nb, h[u]);
+            else v[u] = load_packed<W, PK16>(op.packed_in + P, nb);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; u++) {
+        int64_t c = base + u * 32 + lane;
+        if (c < end) {
+            int64_t P = c * 16;
+            int nb = (int)(op.total - P < 16 ? op.total - P : 16);
+            if (PACK) store_packed<W, PK16>(op.packed_out + P, v[u], nb);
+            else scatter_chunk<W>(op, nodes, blob, P, nb, v[u], h[u]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// segment-major round
+// ---------------------------------------------------------------------------
+// One round: segments [base, base + 32) clipped to s1 (warp-uniform args).
+template <int W, bool PACK>
+__device__ __forceinline__ void seg_round(const Op &op, const DNode *nodes, const char *blob, int64_t nseg_elem,
+                                          const FastDiv &div_nseg, int64_t base, int64_t s1, int lane, Hint &h)
+{
+    using T = typename Word<W>::T;
+    const unsigned FULL = 0xffffffffu;
+    const int nvalid = (int)min((int64_t)32, s1 - base);
+    int64_t disp = 0, len = 0, ps = 0;
+    if (lane < nvalid) {
+        const int64_t k = base + lane;
+        const int64_t e = fdiv(k, div_nseg);
+        disp = e * op.extent;
+        decode_seg(nodes, blob, op.root, k - e * nseg_elem, disp, len, ps, h);
+        ps += e * op.esize;
+    }
+    const int64_t p0 = __shfl_sync(FULL, ps, 0);
+    const int64_t p1 = __shfl_sync(FULL, ps + len, nvalid - 1);
+    const int64_t nwords = (p1 - p0) / W;
+    for (int64_t w0 = 0; w0 < nwords; w0 += 32 * kU) {
+        T v[kU];
+        int64_t ud[kU];
+#pragma unroll
+        for (int u = 0; u < kU; u++) {
+            const int64_t wi = w0 + u * 32 + lane;
+            const int64_t q = p0 + wi * W;
+            int lo = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int cand = lo + step;
+                const int64_t pc = __shfl_sync(FULL, ps, cand & 31);
+                if (cand < nvalid && pc <= q) lo = cand;
+            }
+            ud[u] = __shfl_sync(FULL, disp, lo) + (q - __shfl_sync(FULL, ps, lo));
+            if (wi < nwords) {
+                if (PACK) v[u] = ldw<W>(op.user_in + ud[u]);
+                else v[u] = ldw<W>(op.packed_in + q);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; u++) {
+            const int64_t wi = w0 + u * 32 + lane;
+            if (wi < nwords) {
+                if (PACK) stw<W>(op.packed_out + p0 + wi * W, v[u]);
+                else stw<W>(op.user_out + ud[u], v[u]);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// batch op records
+// ---------------------------------------------------------------------------
+struct BatchOp {
+    Desc d;
+    Op op;
+    int64_t nchunks;
+    int32_t wsel;   // kernel variant (see wsel_of / kSegClass)
+    int32_t soff;   // offset of the descriptor in the group's staged image, or -1
+    // segment-major variants only
+    int64_t nseg_elem;
+    int64_t nsegs;
+    FastDiv div_nseg;
+};
+
+constexpr int kNumClasses = 13;  // 9 chunk-major word classes + 4 segment-major
+
+__host__ __device__ constexpr int wsel_of(int W, bool pk16)
+{
+    return W == 16 ? 0 : W == 8 ? (pk16 ? 1 : 2) : W == 4 ? (pk16 ? 3 : 4) : W == 2 ? (pk16 ? 5 : 6)
+                                                                                 : (pk16 ? 7 : 8);
+}
+
+// segment-major classes: 9 + (W = 8, 4, 2, 1)
+__host__ __device__ constexpr int seg_class(int W)
+{
+    return 9 + (W == 8 ? 0 : W == 4 ? 1 : W == 2 ? 2 : 3);
+}
+
+// ---------------------------------------------------------------------------
+// host helpers
+// ---------------------------------------------------------------------------
+static int sm_count(int dev)
+{
+    static int cache[64];
+    int &c = cache[dev & 63];
+    if (c == 0) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        c = v > 0 ? v : 1;
+    }
+    return c;
+}
+
+template <typename K>
+static int occupancy(K kernel, size_t smem)
+{
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, kThreads, smem) != cudaSuccess ||
+        blocks <= 0) {
+        cudaGetLastError();
+        blocks = 1;
+    }
+    return blocks;
+}
+
+static Desc make_desc(const Committed &c, const char *dblob, size_t *smem)
+{
+    Desc d;
+    d.blob = dblob;
+    d.blob_bytes = c.bytes;
+    d.root = c.root;
+    d.nnodes = c.nnodes;
+    d.pad_ = 0;
+    if (c.bytes <= kSmemBlob) {
+        d.stage = STAGE_BLOB;
+        *smem = (size_t)c.bytes;
+    } else if (c.nnodes <= kMaxSmemNodes) {
+        d.stage = STAGE_NODES;
+        *smem = (size_t)c.nnodes * sizeof(DNode);
+    } else {
+        d.stage = STAGE_NONE;
+        *smem = 0;
+    }
+    return d;
+}
+
+static int64_t p2addr(const void *p)
+{
+    uintptr_t u = (uintptr_t)p;
+    if (u == 0) return 16;
+    uintptr_t low = u & (~u + 1);
+    return low >= 16 ? 16 : (int64_t)low;
+}
+
+static int64_t p2v(int64_t v)
+{
+    if (v == 0) return 16;
+    uint64_t u = (uint64_t)v;
+    uint64_t low = u & (~u + 1);
+    return low >= 16 ? 16 : (int64_t)low;
+}
+
+// copy word for one operation
+static int word_of(const Committed &c, int64_t extent, int64_t count, const void *user, const void *packed)
+{
+    int64_t W = std::min<int64_t>(c.align, std::min(p2addr(user), p2addr(packed)));
+    if (count > 1) W = std::min(W, p2v(extent));
+    return (int)W;
+}
+
+static Op make_op(const Committed &c, int64_t extent, const void *user, void *packed, int64_t count)
+{
+    Op op;
+    op.user_in = (const char *)user;
+    op.user_out = (char *)user;
+    op.packed_in = (const char *)packed;
+    op.packed_out = (char *)packed;
+    op.total = count * c.size;
+    op.esize = c.size;
+    op.extent = extent;
+    op.ediv = c.nodes()[c.root].div_size;
+    op.root = c.root;
+    op.pad_ = 0;
+    return op;
+}
+
+static bool capturing(dte_stream_t stream)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+// Resolve the device descriptor; frees finished deferred descriptors unless
+// the stream is being captured (no event polling inside a capture).
+static int prep(dte_type t, dte_stream_t stream, const char **blob, int *dev)
+{
+    if (!handle_valid(t)) return DTE_ERR_TYPE;
+    if (!t->committed) return DTE_ERR_TYPE;
+    if (!capturing(stream)) reap_deferred();
+    return device_blob(t, blob, dev);
+}
+
+// Fill one op record: copy word, kernel variant (segment-major for short
+// runs moved in sub-16-byte words, as for single ops) and its work size.
+static void fill_batch_op(BatchOp &h, const Committed &c, int64_t extent, const dte_op &o, const char *dblob)
+{
+    size_t smem;
+    h.d = make_desc(c, dblob, &smem);
+    h.soff = -1;
+    h.op = make_op(c, extent, o.user, o.packed, o.count);
+    h.nchunks = (h.op.total + 15) / 16;
+    int W = word_of(c, extent, o.count, o.user, o.packed);
+    if (W < 16 && c.maxrun <= kSegMaxRun) {
+        h.wsel = seg_class(W);
+        h.nseg_elem = c.nseg;
+        h.nsegs = o.count * c.nseg;
+        h.div_nseg = c.nodes()[c.root].div_nseg;
+    } else {
+        h.wsel = wsel_of(W, p2addr(o.packed) >= 16);
+    }
+}
+
+// tiles of an op: 2 KiB steps (chunk-major) or rounds of 32 segments
+static int64_t op_tiles(const BatchOp &h)
+{
+    if (h.wsel >= 9) return (h.nsegs + 31) / 32;
+    return (h.nchunks + kStep - 1) / kStep;
+}
+
+}  // namespace dte

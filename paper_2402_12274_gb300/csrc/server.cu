@@ -1,0 +1,434 @@
+// server.cu -- a device-resident request loop for pack/unpack requests.
+//
+// The paper's progress extension (§7) and generalized-request polling (§2)
+// let asynchronous work advance without the caller blocking; its offloading
+// section (§5) runs communication inside a GPU stream context.  The request
+// loop below is the single-GPU stand-in for that progress engine: a
+// persistent kernel that keeps taking work as the host admits it, so pack and
+// unpack requests of mixed sizes run continuously batched instead of one
+// launch each.
+//
+//   host                                   device (persistent kernel)
+//   ----                                   ---------------------------
+//   submit -> FIFO; admit while ring       warps claim tiles of the oldest
+//   slots and the byte cap allow: write    published request with a CAS on a
+//   the record, then publish (release)     (request, tile) cursor -- never more
+//                                          than is published -- and move them
+//   progress: read completion words        the last warp of a request writes its
+//   (acquire), free capacity, admit more   completion word (release, system scope)
+//
+// Every device wait is bounded: a warp that finds nothing to do polls with
+// __nanosleep and leaves after `idle_limit` empty polls; the host relaunches
+// the loop when work arrives after it left.  A host stop flag ends it at once.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <chrono>
+#include <deque>
+#include <vector>
+
+#include "internal.h"
+#include "move.cuh"
+
+namespace dte {
+
+struct SlotRec {       // one admitted request (pinned host memory)
+    BatchOp op;
+    int32_t kind;      // DTE_BATCH_PACK or DTE_BATCH_UNPACK
+    int32_t pad_;
+    int64_t ntiles;
+};
+
+struct Ctrl {          // pinned host control block
+    int64_t published; // requests visible to the device
+    int64_t stop;      // host asks the loop to leave
+    int64_t pad_[6];
+};
+
+constexpr int kTagBits = 36;  // claim cursor = request << 36 | tile
+constexpr unsigned long long kTileMask = (1ull << kTagBits) - 1;
+
+__device__ __forceinline__ int64_t ld_acquire_sys(const int64_t *p)
+{
+    int64_t v;
+    asm volatile("ld.acquire.sys.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int64_t ld_relaxed_sys(const int64_t *p)
+{
+    int64_t v;
+    asm volatile("ld.relaxed.sys.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_sys(int64_t *p, int64_t v)
+{
+    asm volatile("st.release.sys.global.s64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+template <int W, bool PACK, bool PK16>
+__device__ __noinline__ void serve_chunk_tile(const BatchOp *b, int64_t t, int lane)
+{
+    const char *blob = b->d.blob;
+    const DNode *nodes = reinterpret_cast<const DNode *>(blob + sizeof(BlobHeader));
+    Hint h[kU];
+#pragma unroll
+    for (int u = 0; u < kU; u++) h[u] = Hint{-1, 0};
+    warp_step<W, PACK, PK16>(b->op, nodes, blob, t * kStep, b->nchunks, lane, h);
+}
+
+template <int W, bool PACK>
+__device__ __noinline__ void serve_seg_tile(const BatchOp *b, int64_t t, int lane)
+{
+    const char *blob = b->d.blob;
+    const DNode *nodes = reinterpret_cast<const DNode *>(blob + sizeof(BlobHeader));
+    Hint h{-1, 0};
+    seg_round<W, PACK>(b->op, nodes, blob, b->nseg_elem, b->div_nseg, t * 32, b->nsegs, lane, h);
+}
+
+template <bool PACK>
+__device__ __forceinline__ void serve_tile_dir(const BatchOp *b, int64_t t, int lane)
+{
+    switch (b->wsel) {
+    case 0: serve_chunk_tile<16, PACK, true>(b, t, lane); break;
+    case 1: serve_chunk_tile<8, PACK, true>(b, t, lane); break;
+    case 2: serve_chunk_tile<8, PACK, false>(b, t, lane); break;
+    case 3: serve_chunk_tile<4, PACK, true>(b, t, lane); break;
+    case 4: serve_chunk_tile<4, PACK, false>(b, t, lane); break;
+    case 5: serve_chunk_tile<2, PACK, true>(b, t, lane); break;
+    case 6: serve_chunk_tile<2, PACK, false>(b, t, lane); break;
+    case 7: serve_chunk_tile<1, PACK, true>(b, t, lane); break;
+    case 8: serve_chunk_tile<1, PACK, false>(b, t, lane); break;
+    case 9: serve_seg_tile<8, PACK>(b, t, lane); break;
+    case 10: serve_seg_tile<4, PACK>(b, t, lane); break;
+    case 11: serve_seg_tile<2, PACK>(b, t, lane); break;
+    default: serve_seg_tile<1, PACK>(b, t, lane); break;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 2)
+    serve_kernel(const SlotRec *ring, int64_t mask, Ctrl *ctrl, unsigned long long *claim, unsigned long long *done,
+                 int64_t *comp, int64_t span, int64_t idle_limit)
+{
+    __shared__ BatchOp wop[kWarps];
+    __shared__ int32_t wkind[kWarps];
+    __shared__ int64_t wntiles[kWarps];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    int64_t cached = -1;
+    int64_t idle = 0;
+    for (;;) {
+        int action = 0;  // 0 idle, 1 work, 2 leave, 3 retry
+        int64_t r = 0, t = 0, k = 0;
+        if (lane == 0) {
+            if (ld_relaxed_sys(&ctrl->stop)) {
+                action = 2;
+            } else {
+                unsigned long long w0 = atomicAdd(claim, 0ull);
+                r = (int64_t)(w0 >> kTagBits);
+                t = (int64_t)(w0 & kTileMask);
+                int64_t P = ld_acquire_sys(&ctrl->published);
+                if (r >= P) {
+                    action = 0;
+                } else {
+                    int64_t nt = ld_relaxed_sys(&ring[r & mask].ntiles);
+                    if (t >= nt) {
+                        // request handed out completely: move the cursor on; the
+                        // warp that moves it past an empty request completes it
+                        if (atomicCAS(claim, w0, ((unsigned long long)(r + 1)) << kTagBits) == w0 && nt == 0) {
+                            __threadfence_system();
+                            st_release_sys(comp + (r & mask), r + 1);
+                        }
+                        action = 3;
+                    } else {
+                        k = min(span, nt - t);
+                        unsigned long long w1 = ((unsigned long long)r << kTagBits) | (unsigned long long)(t + k);
+                        action = atomicCAS(claim, w0, w1) == w0 ? 1 : 3;
+                    }
+                }
+            }
+        }
+        action = __shfl_sync(FULL, action, 0);
+        if (action == 2) break;
+        if (action == 3) continue;
+        if (action == 0) {
+            if (++idle > idle_limit) break;  // bounded wait: the host relaunches when needed
+            __nanosleep(1000);
+            continue;
+        }
+        idle = 0;
+        r = __shfl_sync(FULL, r, 0);
+        t = __shfl_sync(FULL, t, 0);
+        k = __shfl_sync(FULL, k, 0);
+        if (r != cached) {
+            // every lane orders its reads of the record after the publication
+            ld_acquire_sys(&ctrl->published);
+            const SlotRec *rec = ring + (r & mask);
+            const int64_t *src = reinterpret_cast<const int64_t *>(&rec->op);
+            int64_t *dst = reinterpret_cast<int64_t *>(&wop[w]);
+            for (int i = lane; i < (int)(sizeof(BatchOp) / 8); i += 32) dst[i] = ld_relaxed_sys(src + i);
+            if (lane == 0) {
+                wkind[w] = (int32_t)ld_relaxed_sys(reinterpret_cast<const int64_t *>(&rec->kind));
+                wntiles[w] = ld_relaxed_sys(&rec->ntiles);
+            }
+            __syncwarp();
+            cached = r;
+        }
+        const bool pack = wkind[w] == DTE_BATCH_PACK;
+        for (int64_t tt = t; tt < t + k; tt++) {
+            if (pack) serve_tile_dir<true>(&wop[w], tt, lane);
+            else serve_tile_dir<false>(&wop[w], tt, lane);
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) {
+            int64_t slot = r & mask;
+            unsigned long long old = atomicAdd(done + slot, (unsigned long long)k);
+            if ((int64_t)old + k == wntiles[w]) {
+                done[slot] = 0;
+                __threadfence_system();
+                st_release_sys(comp + slot, r + 1);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace dte
+
+using namespace dte;
+
+struct dte_server_s {
+    int device = -1;
+    cudaStream_t stream = nullptr;
+    int64_t slots = 0, mask = 0, cap = 0;
+    int ctas_per_sm = 2;
+    int64_t span = 4;
+    int64_t idle_limit = 0;
+    SlotRec *ring = nullptr;  // pinned
+    Ctrl *ctrl = nullptr;     // pinned
+    int64_t *comp = nullptr;  // pinned, one per slot
+    char *dstate = nullptr;   // device: claim cursor + done counters
+    // host bookkeeping
+    struct Pending {
+        BatchOp op;
+        int kind;
+        int64_t ntiles, bytes;
+        std::shared_ptr<Committed> keep;
+    };
+    struct Slot {
+        int64_t req = -1;
+        int64_t bytes = 0;
+        bool open = false;  // admitted, completion not yet accounted
+        std::shared_ptr<Committed> keep;
+    };
+    std::deque<Pending> pending;
+    std::vector<Slot> slot;
+    int64_t next_req = 0;       // next request index to publish
+    int64_t next_ticket = 0;    // tickets are handed out in submission order
+    int64_t oldest_open = 0;    // no request below this is still open
+    int64_t inflight_bytes = 0, inflight = 0;
+    bool launched = false;
+};
+
+namespace dte {
+
+static void server_launch(dte_server s)
+{
+    int sms = 1;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+    unsigned long long *claim = reinterpret_cast<unsigned long long *>(s->dstate);
+    unsigned long long *done = claim + 1;
+    __atomic_store_n(&s->ctrl->stop, (int64_t)0, __ATOMIC_RELEASE);
+    serve_kernel<<<(unsigned)(sms * s->ctas_per_sm), kThreads, 0, s->stream>>>(s->ring, s->mask, s->ctrl, claim, done,
+                                                                              s->comp, s->span, s->idle_limit);
+    s->launched = cudaGetLastError() == cudaSuccess;
+}
+
+// Account completions, admit queued requests, and make sure the loop runs.
+static int server_progress(dte_server s)
+{
+    // completions (completion words are written in any order)
+    for (int64_t r = s->oldest_open; r < s->next_req; r++) {
+        dte_server_s::Slot &sl = s->slot[(size_t)(r & s->mask)];
+        if (!sl.open || sl.req != r) continue;
+        if (__atomic_load_n(s->comp + (r & s->mask), __ATOMIC_ACQUIRE) == r + 1) {
+            sl.open = false;
+            sl.keep.reset();
+            s->inflight_bytes -= sl.bytes;
+            s->inflight--;
+        }
+    }
+    while (s->oldest_open < s->next_req && !s->slot[(size_t)(s->oldest_open & s->mask)].open) s->oldest_open++;
+    // admissions, in submission order
+    while (!s->pending.empty()) {
+        dte_server_s::Pending &p = s->pending.front();
+        dte_server_s::Slot &sl = s->slot[(size_t)(s->next_req & s->mask)];
+        if (sl.open) break;                                               // ring full
+        if (s->inflight > 0 && s->inflight_bytes + p.bytes > s->cap) break;  // byte cap
+        SlotRec &rec = s->ring[s->next_req & s->mask];
+        rec.op = p.op;
+        rec.kind = p.kind;
+        rec.ntiles = p.ntiles;
+        sl.req = s->next_req;
+        sl.bytes = p.bytes;
+        sl.open = true;
+        sl.keep = std::move(p.keep);
+        s->inflight_bytes += p.bytes;
+        s->inflight++;
+        s->next_req++;
+        std::atomic_thread_fence(std::memory_order_release);
+        __atomic_store_n(&s->ctrl->published, s->next_req, __ATOMIC_RELEASE);
+        s->pending.pop_front();
+    }
+    // (re)start the loop if it left while work is outstanding
+    if (s->inflight > 0) {
+        bool running = s->launched && cudaStreamQuery(s->stream) == cudaErrorNotReady;
+        if (!running) {
+            cudaGetLastError();
+            server_launch(s);
+            if (!s->launched) return DTE_ERR_CUDA;
+        }
+    }
+    return DTE_SUCCESS;
+}
+
+static bool ticket_done(dte_server s, int64_t ticket)
+{
+    if (ticket >= s->next_req) return false;  // still queued on the host
+    const dte_server_s::Slot &sl = s->slot[(size_t)(ticket & s->mask)];
+    if (sl.req != ticket) return true;        // its slot was reused: it completed
+    return !sl.open;
+}
+
+}  // namespace dte
+
+extern "C" {
+
+int dte_server_create(const dte_server_config *cfg, dte_server *out)
+{
+    if (!out) return DTE_ERR_ARG;
+    dte_server_config c{1024, (int64_t)8 << 30, 2, 4, 50000};
+    if (cfg) c = *cfg;
+    if (c.ring_slots <= 0 || (c.ring_slots & (c.ring_slots - 1)) || c.ring_slots > (1 << 20)) return DTE_ERR_ARG;
+    if (c.max_inflight_bytes <= 0 || c.ctas_per_sm < 1 || c.ctas_per_sm > 2 || c.span_tiles < 1 ||
+        c.idle_exit_us < 1)
+        return DTE_ERR_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return DTE_ERR_NODEVICE;
+    }
+    auto *s = new dte_server_s();
+    s->device = dev;
+    s->slots = c.ring_slots;
+    s->mask = c.ring_slots - 1;
+    s->cap = c.max_inflight_bytes;
+    s->ctas_per_sm = c.ctas_per_sm;
+    s->span = c.span_tiles;
+    s->idle_limit = c.idle_exit_us;  // one poll sleeps about a microsecond
+    s->slot.resize((size_t)s->slots);
+    bool ok = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaHostAlloc(&s->ring, sizeof(SlotRec) * (size_t)s->slots, cudaHostAllocMapped) == cudaSuccess &&
+              cudaHostAlloc(&s->ctrl, sizeof(Ctrl), cudaHostAllocMapped) == cudaSuccess &&
+              cudaHostAlloc(&s->comp, sizeof(int64_t) * (size_t)s->slots, cudaHostAllocMapped) == cudaSuccess &&
+              cudaMalloc(&s->dstate, sizeof(unsigned long long) * (size_t)(s->slots + 1)) == cudaSuccess &&
+              cudaMemset(s->dstate, 0, sizeof(unsigned long long) * (size_t)(s->slots + 1)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        dte_server_free(&s);
+        return DTE_ERR_NOMEM;
+    }
+    std::memset(s->ring, 0, sizeof(SlotRec) * (size_t)s->slots);
+    std::memset(s->ctrl, 0, sizeof(Ctrl));
+    std::memset(s->comp, 0, sizeof(int64_t) * (size_t)s->slots);
+    *out = s;
+    return DTE_SUCCESS;
+}
+
+int dte_server_submit(dte_server s, int kind, const dte_op *op, int64_t *ticket)
+{
+    try {
+        if (!s || !op || !ticket) return DTE_ERR_ARG;
+        if (kind != DTE_BATCH_PACK && kind != DTE_BATCH_UNPACK) return DTE_ERR_ARG;
+        if (!handle_valid(op->type) || !op->type->committed) return DTE_ERR_TYPE;
+        if (op->count < 0) return DTE_ERR_ARG;
+        int64_t total;
+        if (__builtin_mul_overflow(op->count, op->type->size, &total)) return DTE_ERR_OVERFLOW;
+        if (total > 0 && (!op->user || !op->packed)) return DTE_ERR_ARG;
+        if (kind == DTE_BATCH_UNPACK && total > 0 &&
+            committed_overlaps(*op->type->desc, op->count, op->type->extent()))
+            return DTE_ERR_OVERLAP;
+        dte_server_s::Pending p;
+        std::memset(&p.op, 0, sizeof p.op);
+        p.kind = kind;
+        p.ntiles = 0;
+        p.bytes = 2 * total;
+        if (total > 0) {
+            const char *dblob;
+            int dev;
+            if (int rc = device_blob(op->type, &dblob, &dev)) return rc;
+            if (dev != s->device) return DTE_ERR_ARG;
+            fill_batch_op(p.op, *op->type->desc, op->type->extent(), *op, dblob);
+            p.ntiles = op_tiles(p.op);
+            p.keep = op->type->desc;
+        }
+        *ticket = s->next_ticket++;
+        s->pending.push_back(std::move(p));
+        return server_progress(s);
+    } catch (const Error &e) {
+        return e.code;
+    } catch (...) {
+        return DTE_ERR_NOMEM;
+    }
+}
+
+int dte_server_progress(dte_server s, int64_t *inflight, int64_t *queued)
+{
+    if (!s) return DTE_ERR_ARG;
+    int rc = server_progress(s);
+    if (inflight) *inflight = s->inflight;
+    if (queued) *queued = (int64_t)s->pending.size();
+    return rc;
+}
+
+int dte_server_test(dte_server s, int64_t ticket, int *done)
+{
+    if (!s || !done || ticket < 0 || ticket >= s->next_ticket) return DTE_ERR_ARG;
+    int rc = server_progress(s);
+    *done = ticket_done(s, ticket) ? 1 : 0;
+    return rc;
+}
+
+int dte_server_wait(dte_server s, int64_t ticket, int64_t timeout_us)
+{
+    if (!s || ticket < 0 || ticket >= s->next_ticket || timeout_us < 0) return DTE_ERR_ARG;
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        if (int rc = server_progress(s)) return rc;
+        if (ticket_done(s, ticket)) return DTE_SUCCESS;
+        auto us = std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0).count();
+        if (us > timeout_us) return DTE_ERR_TIMEOUT;
+    }
+}
+
+int dte_server_free(dte_server *sp)
+{
+    if (!sp || !*sp) return DTE_ERR_ARG;
+    dte_server s = *sp;
+    int rc = DTE_SUCCESS;
+    if (s->ctrl) __atomic_store_n(&s->ctrl->stop, (int64_t)1, __ATOMIC_RELEASE);
+    if (s->stream && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = DTE_ERR_CUDA;
+    if (s->stream) cudaStreamDestroy(s->stream);
+    if (s->ring) cudaFreeHost(s->ring);
+    if (s->ctrl) cudaFreeHost(s->ctrl);
+    if (s->comp) cudaFreeHost(s->comp);
+    if (s->dstate) cudaFree(s->dstate);
+    delete s;
+    *sp = nullptr;
+    return rc;
+}
+
+}  // extern "C"

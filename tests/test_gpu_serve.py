@@ -1,0 +1,154 @@
+"""The device-resident request loop: requests of mixed sizes and directions
+that arrive while others run are admitted and batched continuously; each
+result must be byte-identical whether the request ran alone or in the mix,
+and identical to the per-call enqueue path (itself checked against the
+oracle).  Also: admission under a small byte cap, leaving when idle and
+relaunching, and argument errors."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2402_12274_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+import paper_2402_12274_gb300 as dte  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+SENT = 0x6B
+
+
+def make_requests(rng, n, lo=1 << 10, hi=1 << 20):
+    specs = inputs.batch_specs(rng, n, lo=lo, hi=hi)
+    reqs = []
+    for spec, _ in specs:
+        t = dte.Datatype.from_spec(spec).commit()
+        kind = dte.BATCH_PACK if rng.random() < 0.5 else dte.BATCH_UNPACK
+        span = t.true_lb + t.true_extent
+        user = rng.integers(0, 256, span, dtype=np.uint8)
+        packed = rng.integers(0, 256, t.size, dtype=np.uint8)
+        reqs.append(dict(t=t, kind=kind, user=user, packed=packed))
+    return reqs
+
+
+def buffers(reqs):
+    bufs = []
+    for r in reqs:
+        if r["kind"] == dte.BATCH_PACK:
+            u = torch.from_numpy(r["user"]).cuda()
+            p = torch.full((r["t"].size,), SENT, dtype=torch.uint8, device="cuda")
+        else:
+            u = torch.full((r["user"].size,), SENT, dtype=torch.uint8, device="cuda")
+            p = torch.from_numpy(r["packed"]).cuda()
+        bufs.append((u, p))
+    torch.cuda.synchronize()
+    return bufs
+
+
+def outputs(reqs, bufs):
+    torch.cuda.synchronize()
+    return [(p if r["kind"] == dte.BATCH_PACK else u).cpu().numpy() for r, (u, p) in zip(reqs, bufs)]
+
+
+def reference(reqs):
+    bufs = buffers(reqs)
+    s = torch.cuda.current_stream()
+    for r, (u, p) in zip(reqs, bufs):
+        if r["kind"] == dte.BATCH_PACK:
+            dte.pack(u, 1, r["t"], p, 0, s)
+        else:
+            dte.unpack(p, 0, u, 1, r["t"], s)
+    return outputs(reqs, bufs)
+
+
+def test_results_identical_alone_and_in_the_mix():
+    rng = np.random.default_rng(601)
+    reqs = make_requests(rng, 80)
+    reqs += make_requests(rng, 4, lo=8 << 20, hi=16 << 20)
+    ref = reference(reqs)
+    srv = dte.dte_server_create()
+    try:
+        # alone: one request at a time
+        bufs = buffers(reqs)
+        for r, (u, p) in zip(reqs, bufs):
+            tk = dte.dte_server_submit(srv, r["kind"], r["t"].h, 1, u.data_ptr(), p.data_ptr())
+            dte.dte_server_wait(srv, tk)
+        alone = outputs(reqs, bufs)
+        # mixed: everything submitted back to back, with a few short pauses
+        bufs = buffers(reqs)
+        tickets = []
+        for i, (r, (u, p)) in enumerate(zip(reqs, bufs)):
+            tickets.append(dte.dte_server_submit(srv, r["kind"], r["t"].h, 1, u.data_ptr(), p.data_ptr()))
+            if i % 17 == 0:
+                time.sleep(0.0005)
+        for tk in tickets:
+            dte.dte_server_wait(srv, tk)
+        mixed = outputs(reqs, bufs)
+    finally:
+        dte.dte_server_free(srv)
+    for a, b, c in zip(ref, alone, mixed):
+        assert np.array_equal(a, b)
+        assert np.array_equal(a, c)
+
+
+def test_admission_under_a_small_byte_cap():
+    rng = np.random.default_rng(602)
+    reqs = make_requests(rng, 40, lo=16 << 10, hi=64 << 10)
+    ref = reference(reqs)
+    srv = dte.dte_server_create(ring_slots=4, max_inflight_bytes=96 << 10)
+    try:
+        bufs = buffers(reqs)
+        tickets = [dte.dte_server_submit(srv, r["kind"], r["t"].h, 1, u.data_ptr(), p.data_ptr())
+                   for r, (u, p) in zip(reqs, bufs)]
+        inflight, queued = dte.dte_server_progress(srv)
+        assert inflight <= 4 and inflight + queued <= len(reqs)
+        assert queued > 0  # the cap held most requests back on the host
+        for tk in tickets:
+            dte.dte_server_wait(srv, tk)
+        assert dte.dte_server_progress(srv) == (0, 0)
+        got = outputs(reqs, bufs)
+    finally:
+        dte.dte_server_free(srv)
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b)
+
+
+def test_leaves_when_idle_and_relaunches():
+    rng = np.random.default_rng(603)
+    reqs = make_requests(rng, 6)
+    ref = reference(reqs)
+    srv = dte.dte_server_create(idle_exit_us=2000)
+    try:
+        bufs = buffers(reqs)
+        for i, (r, (u, p)) in enumerate(zip(reqs, bufs)):
+            tk = dte.dte_server_submit(srv, r["kind"], r["t"].h, 1, u.data_ptr(), p.data_ptr())
+            dte.dte_server_wait(srv, tk)
+            time.sleep(0.05)  # long enough for the loop to leave
+        got = outputs(reqs, bufs)
+    finally:
+        dte.dte_server_free(srv)
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b)
+
+
+def test_server_argument_errors():
+    with pytest.raises(dte.DteError) as e:
+        dte.dte_server_create(ring_slots=3)
+    assert e.value.code == dte.ERR_ARG
+    srv = dte.dte_server_create()
+    try:
+        ov = dte.Datatype.vector(4, 3, 2, dte.FLOAT32).commit()
+        buf = torch.zeros(256, dtype=torch.uint8, device="cuda")
+        with pytest.raises(dte.DteError) as e:
+            dte.dte_server_submit(srv, dte.BATCH_UNPACK, ov.h, 1, buf.data_ptr(), buf.data_ptr())
+        assert e.value.code == dte.ERR_OVERLAP
+        with pytest.raises(dte.DteError) as e:
+            dte.dte_server_submit(srv, 5, ov.h, 1, buf.data_ptr(), buf.data_ptr())
+        assert e.value.code == dte.ERR_ARG
+        with pytest.raises(dte.DteError):
+            dte.dte_server_wait(srv, 99)
+        # an empty request completes too
+        tk = dte.dte_server_submit(srv, dte.BATCH_PACK, ov.h, 0, 0, 0)
+        dte.dte_server_wait(srv, tk, 2_000_000)
+    finally:
+        dte.dte_server_free(srv)

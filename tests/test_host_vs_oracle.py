@@ -151,3 +151,15 @@ def test_inputs_freed_after_construction():
     c = b.dup()
     del b
     assert c.size == o.size and c.iov_len(-1) == (o.iov_count(), o.size)
+
+
+def test_server_needs_a_device_and_valid_settings():
+    # no CUDA device in a CPU-only run: creation reports it instead of failing later
+    import torch
+    with pytest.raises(dte.DteError) as e:
+        dte.dte_server_create(ring_slots=3)
+    assert e.value.code == dte.ERR_ARG
+    if not torch.cuda.is_available():
+        with pytest.raises(dte.DteError) as e:
+            dte.dte_server_create()
+        assert e.value.code in (dte.ERR_NODEVICE, dte.ERR_CUDA)
