@@ -52,6 +52,7 @@ def parse():
                    help="halo (headline, default) | vector | records | batch | largeblock | autograd | all")
     p.add_argument("--records-blocks", type=int, default=1 << 22)
     p.add_argument("--batch-ops", type=int, default=10000)
+    p.add_argument("--serve-requests", type=int, default=1000)
     return p.parse_args()
 
 
@@ -635,8 +636,82 @@ def run_config_autograd(args):
                                             "backward_us": round(tb * 1e6, 1), "entries": t.size // 4})
 
 
+def run_config_serve(args):
+    """Request loop under Poisson arrivals: pack/unpack requests (50/50) of
+    layouts from the batch generator with sizes log-uniform 1 KiB - 64 MiB,
+    admission cap 8 GiB.  The service rate mu is measured first (all requests
+    submitted at once); then arrivals at rho*mu for rho in {0.5, 0.8, 0.95},
+    latency = host arrival time to observed completion."""
+    import torch
+    import paper_2402_12274_gb300 as dte
+    from paper_2402_12274_gb300 import inputs
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(5)
+    pool = []
+    for spec, _ in inputs.batch_specs(rng, 160, lo=1 << 10, hi=64 << 20):
+        t = dte.Datatype.from_spec(spec).commit()
+        span = t.true_lb + t.true_extent
+        u = torch.empty(span, dtype=torch.uint8, device=dev)
+        u.random_(0, 256)
+        p = torch.empty(t.size, dtype=torch.uint8, device=dev)
+        p.random_(0, 256)
+        pool.append((t, u, p))
+    torch.cuda.synchronize()
+    nreq = args.serve_requests
+    picks = rng.integers(0, len(pool), nreq)
+    kinds = rng.integers(0, 2, nreq)
+    nbytes = np.array([2 * pool[i][0].size for i in picks], dtype=np.float64)
+    srv = dte.dte_server_create(ring_slots=1024, max_inflight_bytes=8 << 30)
+
+    def submit(i):
+        t, u, p = pool[picks[i]]
+        return dte.dte_server_submit(srv, int(kinds[i]), t.h, 1, u.data_ptr(), p.data_ptr())
+
+    # warm up and measure the service rate (everything offered at once)
+    for i in range(min(50, nreq)):
+        dte.dte_server_wait(srv, submit(i), 60_000_000)
+    t0 = time.perf_counter()
+    tks = [submit(i) for i in range(nreq)]
+    for tk in tks:
+        dte.dte_server_wait(srv, tk, 600_000_000)
+    t_all = time.perf_counter() - t0
+    mu = nreq / t_all
+    res = {}
+    for rho in (0.5, 0.8, 0.95):
+        gaps = rng.exponential(1.0 / (rho * mu), nreq)
+        arrive = np.cumsum(gaps)
+        lat = np.zeros(nreq)
+        outstanding = []
+        start = time.perf_counter()
+        i = 0
+        while i < nreq or outstanding:
+            now = time.perf_counter() - start
+            while i < nreq and arrive[i] <= now:
+                outstanding.append((submit(i), i, start + arrive[i]))
+                i += 1
+            dte.dte_server_progress(srv)
+            keep = []
+            for tk, j, ta in outstanding:
+                if dte.dte_server_test(srv, tk):
+                    lat[j] = time.perf_counter() - ta
+                else:
+                    keep.append((tk, j, ta))
+            outstanding = keep
+        wall = time.perf_counter() - start
+        res[str(rho)] = {"p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
+                         "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3),
+                         "throughput_GBs": round(float(nbytes.sum()) / wall / 1e9, 1),
+                         "offered_req_per_s": round(rho * mu, 1)}
+    dte.dte_server_free(srv)
+    _line(f"request loop, {nreq} Poisson-arriving pack/unpack requests of 1 KiB-64 MiB, 8 GiB cap",
+          "p99 latency at rho=0.8 (ms)", res["0.8"]["p99_ms"], "ms",
+          {"higher_is_better": False, "service_rate_req_per_s": round(mu, 1),
+           "service_GBs": round(float(nbytes.sum()) / t_all / 1e9, 1), "by_load": res,
+           "mean_request_bytes_moved": round(float(nbytes.mean()))})
+
+
 CONFIGS = {"vector": run_config_vector, "records": run_config_records, "batch": run_config_batch,
-           "largeblock": run_config_largeblock, "autograd": run_config_autograd}
+           "largeblock": run_config_largeblock, "autograd": run_config_autograd, "serve": run_config_serve}
 
 
 def main():

@@ -45,7 +45,7 @@ struct Ctrl {          // pinned host control block
     int64_t pad_[6];
 };
 
-constexpr int kTagBits = 36;  // claim cursor = request << 36 | tile
+constexpr int kTagBits = 36;  // tile counter = request << 36 | tile
 constexpr unsigned long long kTileMask = (1ull << kTagBits) - 1;
 
 __device__ __forceinline__ int64_t ld_acquire_sys(const int64_t *p)
@@ -107,9 +107,40 @@ __device__ __forceinline__ void serve_tile_dir(const BatchOp *b, int64_t t, int 
     }
 }
 
+// Device state of the loop (device memory, zero at creation); the per-slot
+// tile counters, completion counters and mirrored records follow it.
+struct DevState {
+    unsigned long long cur;   // oldest request still being handed out
+    unsigned long long dpub;  // requests mirrored into device memory
+    int mlock;                // try-lock of the warp mirroring new requests
+    int pad_;
+};
+
+__device__ __forceinline__ unsigned long long ld_relaxed_gpu(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Warps claim tiles with fetch-adds on the slot counter of the oldest request
+// being handed out; a counter holds (request << 36 | next tile), so a warp
+// whose view of the oldest request is stale still learns from the counter
+// which request its tiles belong to.  Counters are re-tagged only when a
+// request is mirrored into its slot, which the host allows only after the
+// slot's previous request completed, so no claimed tile is ever lost.  The
+// host side of the ring (pinned memory) is touched only by the warp that
+// mirrors new requests and by idle warps.
 __global__ void __launch_bounds__(kThreads, 2)
-    serve_kernel(const SlotRec *ring, int64_t mask, Ctrl *ctrl, unsigned long long *claim, unsigned long long *done,
-                 int64_t *comp, int64_t span, int64_t idle_limit)
+    serve_kernel(const SlotRec *ring, int64_t mask, Ctrl *ctrl, DevState *st, unsigned long long *ctr,
+                 unsigned long long *done, SlotRec *dring, int64_t *comp, int64_t span, int64_t idle_budget_ns)
 {
     __shared__ BatchOp wop[kWarps];
     __shared__ int32_t wkind[kWarps];
@@ -118,34 +149,48 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
     int64_t cached = -1;
-    int64_t idle = 0;
+    int64_t idle_ns = 0;
+    unsigned backoff = 256;
     for (;;) {
-        int action = 0;  // 0 idle, 1 work, 2 leave, 3 retry
+        int action = 0;  // 0 idle, 1 work, 2 leave, 3 retry, 4 mirror
         int64_t r = 0, t = 0, k = 0;
         if (lane == 0) {
-            if (ld_relaxed_sys(&ctrl->stop)) {
-                action = 2;
-            } else {
-                unsigned long long w0 = atomicAdd(claim, 0ull);
-                r = (int64_t)(w0 >> kTagBits);
-                t = (int64_t)(w0 & kTileMask);
-                int64_t P = ld_acquire_sys(&ctrl->published);
-                if (r >= P) {
-                    action = 0;
+            const unsigned long long c = ld_relaxed_gpu(&st->cur);
+            const unsigned long long pub = ld_acquire_gpu(&st->dpub);
+            if (c >= pub) {
+                const int64_t P = ld_acquire_sys(&ctrl->published);
+                if ((unsigned long long)P > pub) {
+                    action = atomicCAS(&st->mlock, 0, 1) == 0 ? 4 : 3;
+                    r = P;
                 } else {
-                    int64_t nt = ld_relaxed_sys(&ring[r & mask].ntiles);
-                    if (t >= nt) {
-                        // request handed out completely: move the cursor on; the
-                        // warp that moves it past an empty request completes it
-                        if (atomicCAS(claim, w0, ((unsigned long long)(r + 1)) << kTagBits) == w0 && nt == 0) {
-                            __threadfence_system();
-                            st_release_sys(comp + (r & mask), r + 1);
-                        }
-                        action = 3;
-                    } else {
-                        k = min(span, nt - t);
-                        unsigned long long w1 = ((unsigned long long)r << kTagBits) | (unsigned long long)(t + k);
-                        action = atomicCAS(claim, w0, w1) == w0 ? 1 : 3;
+                    action = ld_relaxed_sys(&ctrl->stop) ? 2 : 0;
+                }
+            } else {
+                const int64_t slot = (int64_t)(c & (unsigned long long)mask);
+                const unsigned long long v = atomicAdd(ctr + slot, (unsigned long long)span);
+                __threadfence();
+                const int64_t tag = (int64_t)(v >> kTagBits);
+                t = (int64_t)(v & kTileMask);
+                const int64_t nt = (int64_t)ld_relaxed_gpu(reinterpret_cast<const unsigned long long *>(&dring[slot].ntiles));
+                if (t >= nt) {
+                    atomicMax(&st->cur, (unsigned long long)(tag + 1));
+                    if (t == 0 && nt == 0) {  // empty request: its first claimer completes it
+                        __threadfence_system();
+                        st_release_sys(comp + slot, tag + 1);
+                    }
+                    action = 3;
+                } else {
+                    r = tag;
+                    k = min(span, nt - t);
+                    action = 1;
+                    if (r != cached) {
+                        // the record, read past L1 (a slot is rewritten for each
+                        // request) and after the counter that announced it
+                        const unsigned long long *src = reinterpret_cast<const unsigned long long *>(&dring[slot]);
+                        unsigned long long *dst = reinterpret_cast<unsigned long long *>(&wop[w]);
+                        for (int i = 0; i < (int)(sizeof(BatchOp) / 8); i++) dst[i] = ld_relaxed_gpu(src + i);
+                        wkind[w] = (int32_t)ld_relaxed_gpu(src + sizeof(BatchOp) / 8);
+                        wntiles[w] = nt;
                     }
                 }
             }
@@ -154,28 +199,40 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (action == 2) break;
         if (action == 3) continue;
         if (action == 0) {
-            if (++idle > idle_limit) break;  // bounded wait: the host relaunches when needed
-            __nanosleep(1000);
+            idle_ns += backoff;
+            if (idle_ns > idle_budget_ns) break;  // bounded: the host relaunches when work arrives
+            __nanosleep(backoff);
+            backoff = backoff < 8192 ? backoff * 2 : 8192;
             continue;
         }
-        idle = 0;
+        idle_ns = 0;
+        backoff = 256;
         r = __shfl_sync(FULL, r, 0);
-        t = __shfl_sync(FULL, t, 0);
-        k = __shfl_sync(FULL, k, 0);
-        if (r != cached) {
-            // every lane orders its reads of the record after the publication
-            ld_acquire_sys(&ctrl->published);
-            const SlotRec *rec = ring + (r & mask);
-            const int64_t *src = reinterpret_cast<const int64_t *>(&rec->op);
-            int64_t *dst = reinterpret_cast<int64_t *>(&wop[w]);
-            for (int i = lane; i < (int)(sizeof(BatchOp) / 8); i += 32) dst[i] = ld_relaxed_sys(src + i);
+        if (action == 4) {
+            // mirror requests [dpub, P) from pinned host memory into device memory
+            const int64_t from = (int64_t)ld_relaxed_gpu(&st->dpub);
+            ld_acquire_sys(&ctrl->published);  // each lane orders its reads after the publication
+            for (int64_t q = from; q < r; q++) {
+                const int64_t *src = reinterpret_cast<const int64_t *>(ring + (q & mask));
+                int64_t *dst = reinterpret_cast<int64_t *>(dring + (q & mask));
+                for (int i = lane; i < (int)(sizeof(SlotRec) / 8); i += 32) dst[i] = ld_relaxed_sys(src + i);
+            }
+            __threadfence();
+            __syncwarp();
             if (lane == 0) {
-                wkind[w] = (int32_t)ld_relaxed_sys(reinterpret_cast<const int64_t *>(&rec->kind));
-                wntiles[w] = ld_relaxed_sys(&rec->ntiles);
+                for (int64_t q = from; q < r; q++) ctr[q & mask] = ((unsigned long long)q) << kTagBits;
+                __threadfence();
+                atomicExch(&st->dpub, (unsigned long long)r);
+                __threadfence();
+                atomicExch(&st->mlock, 0);
             }
             __syncwarp();
-            cached = r;
+            continue;
         }
+        t = __shfl_sync(FULL, t, 0);
+        k = __shfl_sync(FULL, k, 0);
+        __syncwarp();
+        cached = r;
         const bool pack = wkind[w] == DTE_BATCH_PACK;
         for (int64_t tt = t; tt < t + k; tt++) {
             if (pack) serve_tile_dir<true>(&wop[w], tt, lane);
@@ -184,8 +241,8 @@ __global__ void __launch_bounds__(kThreads, 2)
         __threadfence();
         __syncwarp();
         if (lane == 0) {
-            int64_t slot = r & mask;
-            unsigned long long old = atomicAdd(done + slot, (unsigned long long)k);
+            const int64_t slot = r & mask;
+            const unsigned long long old = atomicAdd(done + slot, (unsigned long long)k);
             if ((int64_t)old + k == wntiles[w]) {
                 done[slot] = 0;
                 __threadfence_system();
@@ -210,7 +267,7 @@ struct dte_server_s {
     SlotRec *ring = nullptr;  // pinned
     Ctrl *ctrl = nullptr;     // pinned
     int64_t *comp = nullptr;  // pinned, one per slot
-    char *dstate = nullptr;   // device: claim cursor + done counters
+    char *dstate = nullptr;   // device: DevState, tile counters, done counters, mirrored records
     // host bookkeeping
     struct Pending {
         BatchOp op;
@@ -235,15 +292,22 @@ struct dte_server_s {
 
 namespace dte {
 
+static size_t dstate_bytes(int64_t slots)
+{
+    return sizeof(DevState) + (size_t)slots * (2 * sizeof(unsigned long long) + sizeof(SlotRec));
+}
+
 static void server_launch(dte_server s)
 {
     int sms = 1;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
-    unsigned long long *claim = reinterpret_cast<unsigned long long *>(s->dstate);
-    unsigned long long *done = claim + 1;
+    DevState *st = reinterpret_cast<DevState *>(s->dstate);
+    unsigned long long *ctr = reinterpret_cast<unsigned long long *>(s->dstate + sizeof(DevState));
+    unsigned long long *done = ctr + s->slots;
+    SlotRec *dring = reinterpret_cast<SlotRec *>(done + s->slots);
     __atomic_store_n(&s->ctrl->stop, (int64_t)0, __ATOMIC_RELEASE);
-    serve_kernel<<<(unsigned)(sms * s->ctas_per_sm), kThreads, 0, s->stream>>>(s->ring, s->mask, s->ctrl, claim, done,
-                                                                              s->comp, s->span, s->idle_limit);
+    serve_kernel<<<(unsigned)(sms * s->ctas_per_sm), kThreads, 0, s->stream>>>(
+        s->ring, s->mask, s->ctrl, st, ctr, done, dring, s->comp, s->span, s->idle_limit * 1000);
     s->launched = cudaGetLastError() == cudaSuccess;
 }
 
@@ -328,14 +392,14 @@ int dte_server_create(const dte_server_config *cfg, dte_server *out)
     s->cap = c.max_inflight_bytes;
     s->ctas_per_sm = c.ctas_per_sm;
     s->span = c.span_tiles;
-    s->idle_limit = c.idle_exit_us;  // one poll sleeps about a microsecond
+    s->idle_limit = c.idle_exit_us;
     s->slot.resize((size_t)s->slots);
     bool ok = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) == cudaSuccess &&
               cudaHostAlloc(&s->ring, sizeof(SlotRec) * (size_t)s->slots, cudaHostAllocMapped) == cudaSuccess &&
               cudaHostAlloc(&s->ctrl, sizeof(Ctrl), cudaHostAllocMapped) == cudaSuccess &&
               cudaHostAlloc(&s->comp, sizeof(int64_t) * (size_t)s->slots, cudaHostAllocMapped) == cudaSuccess &&
-              cudaMalloc(&s->dstate, sizeof(unsigned long long) * (size_t)(s->slots + 1)) == cudaSuccess &&
-              cudaMemset(s->dstate, 0, sizeof(unsigned long long) * (size_t)(s->slots + 1)) == cudaSuccess;
+              cudaMalloc(&s->dstate, dstate_bytes(s->slots)) == cudaSuccess &&
+              cudaMemset(s->dstate, 0, dstate_bytes(s->slots)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         dte_server_free(&s);
