@@ -380,7 +380,7 @@ def run_dte(args):
     tdom = max(mp, mu)
     per_launch = size
     achieved = ALG_FACTOR * per_launch / tdom / 1e9
-    kname = "dte::move_kernel<16, 1, 1>" if dom == "pack" else "dte::batch_kernel<0>"
+    kname = "dte::move_kernel<16, 1, 1>" if dom == "pack" else "dte::batch_kernel<16, 0, 1>"
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic_from_profile(kname),
             "kernel": kname, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
