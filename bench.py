@@ -189,6 +189,24 @@ class L2Flush:
         torch.sum(self.r, dim=0, out=self.out)
 
 
+def max_over_ranks(seconds: float, world: int, dev=None) -> float:
+    """The slowest rank's time (every rank gets it); a no-op on one rank.
+    Ranks are independent replicas, so this is the only collective."""
+    if world <= 1:
+        return seconds
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_throughput(bytes_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job GB/s: every rank moved bytes_per_rank in at most `seconds`."""
+    return bytes_per_rank * world / seconds / 1e9
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -325,14 +343,9 @@ def run_dte(args):
     torch.cuda.synchronize()
     t_pack = np.array([ev[i][0].elapsed_time(ev[i][1]) for i in range(K)]) * 1e-3
     t_unpack = np.array([ev[i][1].elapsed_time(ev[i][2]) for i in range(K)]) * 1e-3
-    total = float((t_pack + t_unpack).sum())
-    if world > 1:
-        tt = torch.tensor([total], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total = float(tt.item())
-        dist.barrier()
+    total = max_over_ranks(float((t_pack + t_unpack).sum()), world, dev)
     alg_step = 2 * ALG_FACTOR * size
-    value = alg_step * K * world / total / 1e9
+    value = job_throughput(alg_step * K, world, total)
 
     # e2e: the same step through the C ABI on pinned host grids (the kernels
     # read and write host memory over NVLink-C2C; no staging copies)
@@ -359,12 +372,8 @@ def run_dte(args):
                 step_host()
             e1.record(stream)
         stream.synchronize()
-        te = e0.elapsed_time(e1) * 1e-3
-        if world > 1:
-            tt = torch.tensor([te], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
-        e2e = {"value": round(alg_step * ke * world / te / 1e9, 3), "unit": "GB/s",
+        te = max_over_ranks(e0.elapsed_time(e1) * 1e-3, world, dev)
+        e2e = {"value": round(job_throughput(alg_step * ke, world, te), 3), "unit": "GB/s",
                "h2d_bytes_per_step": size, "d2h_bytes_per_step": size,
                "mode": "pinned host grids accessed by the kernels (zero-copy over NVLink-C2C)"}
 
