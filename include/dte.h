@@ -86,6 +86,8 @@ enum dte_basic {
 };
 
 enum dte_order { DTE_ORDER_C = 0, DTE_ORDER_FORTRAN = 1 };
+enum dte_distribute { DTE_DISTRIBUTE_BLOCK = 0, DTE_DISTRIBUTE_CYCLIC = 1, DTE_DISTRIBUTE_NONE = 2 };
+#define DTE_DISTRIBUTE_DFLT_DARG (-1)
 
 /* Human-readable name of an error code (static storage, never NULL). */
 DTE_API const char *dte_error_string(int code);
@@ -140,6 +142,18 @@ DTE_API int dte_type_struct(int64_t count, const int64_t *bl, const int64_t *dis
  * extent = prod(sizes) * extent(old).  ndims <= 32. */
 DTE_API int dte_type_subarray(int ndims, const int64_t *sizes, const int64_t *subsizes,
                       const int64_t *starts, int order, dte_type old, dte_type *out);
+
+/* Distributed array (MPI's darray): the part of an ndims-dimensional global
+ * array (gsizes, elements of old) owned by process `rank` of a row-major
+ * process grid psizes (prod(psizes) == size).  Per dimension, distribs[d] is
+ * DTE_DISTRIBUTE_BLOCK (one block of dargs[d] indices, default
+ * ceil(g/p)), DTE_DISTRIBUTE_CYCLIC (blocks of dargs[d], default 1, dealt
+ * round-robin) or DTE_DISTRIBUTE_NONE (the whole dimension; psizes[d] must
+ * be 1); DTE_DISTRIBUTE_DFLT_DARG selects the default.  Elements follow the
+ * array order (C or Fortran); lb = 0, extent = prod(gsizes)*extent(old). */
+DTE_API int dte_type_darray(int size, int rank, int ndims, const int64_t *gsizes, const int *distribs,
+                            const int64_t *dargs, const int64_t *psizes, int order, dte_type old,
+                            dte_type *out);
 
 /* Same typemap as old with lb and extent replaced. */
 DTE_API int dte_type_resized(dte_type old, int64_t lb, int64_t extent, dte_type *out);

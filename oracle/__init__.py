@@ -60,6 +60,7 @@ def lib():
             "or_struct": [_i64, _pi64, _pi64, C.POINTER(_p)],
             "or_subarray": [C.c_int, _pi64, _pi64, _pi64, C.c_int, _p],
             "or_resized": [_p, _i64, _i64],
+            "or_darray": [C.c_int, C.c_int, C.c_int, _pi64, C.POINTER(C.c_int), _pi64, _pi64, C.c_int, _p],
         }.items():
             f = getattr(L, name)
             f.argtypes = args
@@ -271,6 +272,18 @@ def subarray(sizes, subsizes, starts, old: OType, order: int = ORDER_C) -> OType
     return OType(lib().or_subarray(s.size, ps, pu, pt, order, old.h))
 
 
+DIST_BLOCK, DIST_CYCLIC, DIST_NONE = 0, 1, 2
+DFLT_DARG = -1
+
+
+def darray(size, rank, gsizes, distribs, dargs, psizes, old: OType, order: int = ORDER_C) -> OType:
+    g, pg = _arr(gsizes)
+    a, pa = _arr(dargs)
+    ps, pps = _arr(psizes)
+    dist = (C.c_int * len(distribs))(*[int(x) for x in distribs])
+    return OType(lib().or_darray(size, rank, g.size, pg, dist, pa, pps, order, old.h))
+
+
 def resized(old: OType, lb: int, extent: int) -> OType:
     return OType(lib().or_resized(old.h, lb, extent))
 
@@ -305,4 +318,7 @@ def from_spec(spec) -> OType:
         return subarray(spec[1], spec[2], spec[3], from_spec(spec[5]), spec[4])
     if k == "resized":
         return resized(from_spec(spec[3]), spec[1], spec[2])
+    if k == "darray":
+        _, size, rank, gs, dist, dargs, ps, order, child = spec
+        return darray(size, rank, gs, dist, dargs, ps, from_spec(child), order)
     raise ValueError(f"unknown spec kind {k!r}")

@@ -35,7 +35,7 @@
 
 enum {
     K_BASIC, K_CONTIG, K_VECTOR, K_HVECTOR, K_INDEXED, K_HINDEXED,
-    K_STRUCT, K_SUBARRAY, K_RESIZED
+    K_STRUCT, K_SUBARRAY, K_RESIZED, K_DARRAY
 };
 
 #define OR_MAXDIMS 32
@@ -50,6 +50,7 @@ struct or_type {
     or_type *old;                        /* everything but basic/struct */
     int ndims, order;                    /* subarray */
     int64_t sizes[OR_MAXDIMS], subsizes[OR_MAXDIMS], starts[OR_MAXDIMS];
+    int64_t *owned[OR_MAXDIMS], nowned[OR_MAXDIMS];   /* darray: owned indices per dim */
     int64_t basic_size;
     /* derived attributes */
     int64_t size, nbasic, lb, ub, true_lb, true_ub, align;
@@ -127,6 +128,40 @@ static void for_each_copy(const or_type *t, copy_fn fn, void *ctx)
             } else {
                 for (d = 0; d < n; d++) {
                     if (++idx[d] < t->subsizes[d]) break;
+                    idx[d] = 0;
+                }
+                if (d == n) d = -1;
+            }
+            if (d < 0) return;
+        }
+        break;
+    }
+    case K_DARRAY: {
+        /* Owned elements of the global array in C or Fortran order; element
+         * idx sits at the linear index of (owned[0][idx0], ...) in the global
+         * array, times extent(old). */
+        int n = t->ndims, d;
+        int64_t idx[OR_MAXDIMS];
+        for (d = 0; d < n; d++) {
+            if (t->nowned[d] == 0) return;
+            idx[d] = 0;
+        }
+        for (;;) {
+            int64_t lin = 0;
+            if (t->order == OR_ORDER_C) {
+                for (d = 0; d < n; d++) lin = lin * t->sizes[d] + t->owned[d][idx[d]];
+            } else {
+                for (d = n - 1; d >= 0; d--) lin = lin * t->sizes[d] + t->owned[d][idx[d]];
+            }
+            fn(ctx, lin * ext_of(t->old), t->old);
+            if (t->order == OR_ORDER_C) {
+                for (d = n - 1; d >= 0; d--) {
+                    if (++idx[d] < t->nowned[d]) break;
+                    idx[d] = 0;
+                }
+            } else {
+                for (d = 0; d < n; d++) {
+                    if (++idx[d] < t->nowned[d]) break;
                     idx[d] = 0;
                 }
                 if (d == n) d = -1;
@@ -360,6 +395,64 @@ or_type *or_subarray(int ndims, const int64_t *sizes, const int64_t *subsizes,
     return t;
 }
 
+/* Distributed array: the block of a global array (gsizes) that process
+ * `rank` of a row-major process grid (psizes) owns, per dimension BLOCK
+ * (block size darg, default ceil(g/p)), CYCLIC (blocks of darg, default 1,
+ * dealt round-robin) or NONE (whole dimension, p must be 1). */
+or_type *or_darray(int size, int rank, int ndims, const int64_t *gsizes, const int *distribs,
+                   const int64_t *dargs, const int64_t *psizes, int order, or_type *old)
+{
+    or_type *t;
+    int d;
+    int64_t full = 1, nproc = 1, r, coord[OR_MAXDIMS];
+    if (ndims <= 0 || ndims > OR_MAXDIMS || !old || size <= 0 || rank < 0 || rank >= size) return NULL;
+    if (order != OR_ORDER_C && order != OR_ORDER_F) return NULL;
+    for (d = 0; d < ndims; d++) {
+        if (gsizes[d] <= 0 || psizes[d] <= 0) return NULL;
+        nproc *= psizes[d];
+        full *= gsizes[d];
+    }
+    if (nproc != size) return NULL;
+    r = rank;
+    for (d = ndims - 1; d >= 0; d--) {  /* process grid is row-major */
+        coord[d] = r % psizes[d];
+        r /= psizes[d];
+    }
+    t = new_type(K_DARRAY);
+    if (!t) return NULL;
+    t->ndims = ndims;
+    t->order = order;
+    for (d = 0; d < ndims; d++) {
+        int64_t g = gsizes[d], p = psizes[d], c = coord[d], b, i, n = 0;
+        t->sizes[d] = g;
+        t->owned[d] = (int64_t *)malloc((size_t)g * sizeof(int64_t));
+        if (!t->owned[d]) { or_free(t); return NULL; }
+        if (distribs[d] == OR_DIST_NONE) {
+            if (p != 1) { or_free(t); return NULL; }
+            for (i = 0; i < g; i++) t->owned[d][n++] = i;
+        } else if (distribs[d] == OR_DIST_BLOCK) {
+            b = dargs[d] == OR_DFLT_DARG ? (g + p - 1) / p : dargs[d];
+            if (b <= 0 || b * p < g) { or_free(t); return NULL; }
+            for (i = c * b; i < c * b + b && i < g; i++) t->owned[d][n++] = i;
+        } else if (distribs[d] == OR_DIST_CYCLIC) {
+            b = dargs[d] == OR_DFLT_DARG ? 1 : dargs[d];
+            if (b <= 0) { or_free(t); return NULL; }
+            for (i = 0; i < g; i++)
+                if ((i / b) % p == c) t->owned[d][n++] = i;
+        } else {
+            or_free(t);
+            return NULL;
+        }
+        t->nowned[d] = n;
+    }
+    t->old = old; old->refs++;
+    finish_attrs(t);
+    t->lb = 0;
+    t->ub = full * ext_of(old);
+    t->lb_explicit = t->ub_explicit = 1;
+    return t;
+}
+
 or_type *or_resized(or_type *old, int64_t lb, int64_t extent)
 {
     or_type *t;
@@ -385,6 +478,7 @@ void or_free(or_type *t)
     }
     free(t->bls);
     free(t->disps);
+    for (i = 0; i < OR_MAXDIMS; i++) free(t->owned[i]);
     free(t);
 }
 

@@ -11,7 +11,8 @@
  *   - the typemap of a derived datatype built from the MPI constructors the
  *     paper uses (contiguous, subarray) and the usual companions (vector,
  *     hvector, indexed, hindexed, indexed_block, hindexed_block, struct,
- *     resized), expanded one basic entry at a time in constructor order;
+ *     resized, darray), expanded one basic entry at a time in constructor
+ *     order;
  *   - size, lb/ub/extent and true lb/extent by the MPI constructor rules;
  *   - the segment ("iov") list: the typemap walked in order, an entry merged
  *     into the current segment only when it starts exactly where that segment
@@ -37,6 +38,8 @@ typedef struct or_type or_type;
 
 enum { OR_OK = 0, OR_EARG = -1, OR_ENOMEM = -2, OR_EOVERLAP = -3 };
 enum { OR_ORDER_C = 0, OR_ORDER_F = 1 };
+enum { OR_DIST_BLOCK = 0, OR_DIST_CYCLIC = 1, OR_DIST_NONE = 2 };
+#define OR_DFLT_DARG (-1)
 
 /* Constructors.  Each returns NULL on an invalid argument.  Children are
  * reference counted: a constructor takes a reference on each old type, and
@@ -53,6 +56,8 @@ or_type *or_hindexed_block(int64_t count, int64_t bl, const int64_t *disp_bytes,
 or_type *or_struct(int64_t count, const int64_t *bl, const int64_t *disp_bytes, or_type *const *types);
 or_type *or_subarray(int ndims, const int64_t *sizes, const int64_t *subsizes,
                      const int64_t *starts, int order, or_type *old);
+or_type *or_darray(int size, int rank, int ndims, const int64_t *gsizes, const int *distribs,
+                   const int64_t *dargs, const int64_t *psizes, int order, or_type *old);
 or_type *or_resized(or_type *old, int64_t lb, int64_t extent);
 void or_free(or_type *t);
 

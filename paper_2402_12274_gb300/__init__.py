@@ -87,6 +87,8 @@ _SIGS = {
     "dte_type_struct": ([_i64, _pi64, _pi64, _pp, _pp], C.c_int),
     "dte_type_subarray": ([C.c_int, _pi64, _pi64, _pi64, C.c_int, _p, _pp], C.c_int),
     "dte_type_resized": ([_p, _i64, _i64, _pp], C.c_int),
+    "dte_type_darray": ([C.c_int, C.c_int, C.c_int, _pi64, C.POINTER(C.c_int), _pi64, _pi64, C.c_int, _p, _pp],
+                        C.c_int),
     "dte_type_dup": ([_p, _pp], C.c_int),
     "dte_type_commit": ([_pp], C.c_int),
     "dte_type_free": ([_pp], C.c_int),
@@ -218,6 +220,20 @@ def dte_type_subarray(sizes, subsizes, starts, order: int, old: int) -> int:
     if not (n == n2 == n3):
         raise ValueError("subarray arrays differ in length")
     return _ctor("dte_type_subarray", n, ps, pu, pt, order, old)
+
+
+DISTRIBUTE_BLOCK, DISTRIBUTE_CYCLIC, DISTRIBUTE_NONE = 0, 1, 2
+DISTRIBUTE_DFLT_DARG = -1
+
+
+def dte_type_darray(size: int, rank: int, gsizes, distribs, dargs, psizes, order: int, old: int) -> int:
+    kg, pg, n = _int64_ptr(gsizes)
+    ka, pa, n2 = _int64_ptr(dargs)
+    kp, pp, n3 = _int64_ptr(psizes)
+    if not (n == n2 == n3 == len(distribs)):
+        raise ValueError("darray arrays differ in length")
+    dist = (C.c_int * max(n, 1))(*[int(x) for x in distribs])
+    return _ctor("dte_type_darray", size, rank, n, pg, dist, pa, pp, order, old)
 
 
 def dte_type_resized(old: int, lb: int, extent: int) -> int:
@@ -525,6 +541,11 @@ class Datatype:
         return Datatype(dte_type_subarray(sizes, subsizes, starts, order, int(old)))
     @staticmethod
     def resized(old, lb, extent): return Datatype(dte_type_resized(int(old), lb, extent))
+
+    @staticmethod
+    def darray(size, rank, gsizes, distribs, dargs, psizes, old, order=ORDER_C):
+        return Datatype(dte_type_darray(size, rank, gsizes, distribs, dargs, psizes, order, int(old)))
+
     def dup(self): return Datatype(dte_type_dup(self.h))
 
     @staticmethod
@@ -555,6 +576,9 @@ class Datatype:
             return Datatype.subarray(spec[1], spec[2], spec[3], f(spec[5]), spec[4])
         if k == "resized":
             return Datatype.resized(f(spec[3]), spec[1], spec[2])
+        if k == "darray":
+            _, size, rank, gs, dist, dargs, ps, order, child = spec
+            return Datatype.darray(size, rank, gs, dist, dargs, ps, f(child), order)
         raise ValueError(f"unknown spec kind {k!r}")
 
 

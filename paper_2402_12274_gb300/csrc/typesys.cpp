@@ -1002,6 +1002,71 @@ int dte_type_subarray(int ndims, const int64_t *sizes, const int64_t *subsizes, 
     DTE_CATCH
 }
 
+int dte_type_darray(int size, int rank, int ndims, const int64_t *gsizes, const int *distribs, const int64_t *dargs,
+                    const int64_t *psizes, int order, dte_type old, dte_type *out)
+{
+    DTE_TRY
+    if (int rc = check_old(old)) return rc;
+    if (!out || ndims <= 0 || ndims > 32 || !gsizes || !distribs || !dargs || !psizes) return DTE_ERR_ARG;
+    if (size <= 0 || rank < 0 || rank >= size) return DTE_ERR_ARG;
+    if (order != DTE_ORDER_C && order != DTE_ORDER_FORTRAN) return DTE_ERR_ARG;
+    int64_t nproc = 1;
+    for (int d = 0; d < ndims; d++) {
+        if (gsizes[d] <= 0 || psizes[d] <= 0) return DTE_ERR_ARG;
+        nproc = mul_ck(nproc, psizes[d]);
+    }
+    if (nproc != size) return DTE_ERR_ARG;
+    int64_t coord[32];
+    int64_t r = rank;
+    for (int d = ndims - 1; d >= 0; d--) {  // the process grid is row-major
+        coord[d] = r % psizes[d];
+        r /= psizes[d];
+    }
+    int64_t e = old->extent();
+    int64_t stride[32];
+    int64_t full = 1;
+    if (order == DTE_ORDER_C) {
+        for (int d = ndims - 1; d >= 0; d--) { stride[d] = mul_ck(full, e); full = mul_ck(full, gsizes[d]); }
+    } else {
+        for (int d = 0; d < ndims; d++) { stride[d] = mul_ck(full, e); full = mul_ck(full, gsizes[d]); }
+    }
+    // per dimension, the owned index blocks of this process; nest from the
+    // fastest dimension outwards
+    NP node = old->node;
+    bool any = true;
+    for (int s = 0; s < ndims; s++) {
+        int d = order == DTE_ORDER_C ? ndims - 1 - s : s;
+        int64_t g = gsizes[d], p = psizes[d], c = coord[d];
+        std::vector<Entry> ent;
+        if (distribs[d] == DTE_DISTRIBUTE_NONE) {
+            if (p != 1) return DTE_ERR_ARG;
+            ent.push_back(Entry{0, g, node, stride[d]});
+        } else if (distribs[d] == DTE_DISTRIBUTE_BLOCK) {
+            int64_t b = dargs[d] == DTE_DISTRIBUTE_DFLT_DARG ? (g + p - 1) / p : dargs[d];
+            if (b <= 0 || mul_ck(b, p) < g) return DTE_ERR_ARG;
+            int64_t lo = mul_ck(c, b), hi = std::min(add_ck(lo, b), g);
+            if (lo < hi) ent.push_back(Entry{mul_ck(lo, stride[d]), hi - lo, node, stride[d]});
+        } else if (distribs[d] == DTE_DISTRIBUTE_CYCLIC) {
+            int64_t b = dargs[d] == DTE_DISTRIBUTE_DFLT_DARG ? 1 : dargs[d];
+            if (b <= 0) return DTE_ERR_ARG;
+            for (int64_t lo = mul_ck(c, b); lo < g; lo = add_ck(lo, mul_ck(p, b)))
+                ent.push_back(Entry{mul_ck(lo, stride[d]), std::min(b, g - lo), node, stride[d]});
+        } else {
+            return DTE_ERR_ARG;
+        }
+        any = any && !ent.empty();
+        node = make_list(std::move(ent));
+    }
+    Acc a;
+    if (any && (old->nonempty || old->lb_x || old->ub_x)) a.align = old->align;
+    a.lbx = a.ubx = true;
+    a.lb_x = 0;
+    a.ub_x = mul_ck(full, e);
+    *out = new_type(a, node, false);
+    return DTE_SUCCESS;
+    DTE_CATCH
+}
+
 int dte_type_resized(dte_type old, int64_t lb, int64_t extent, dte_type *out)
 {
     DTE_TRY

@@ -17,6 +17,8 @@ with their own constructors:
     ("struct", bl[], disp_bytes[], [children])
     ("subarray", sizes[], subsizes[], starts[], order, child)   # order 0 = C, 1 = Fortran
     ("resized", lb, extent, child)
+    ("darray", size, rank, gsizes[], distribs[], dargs[], psizes[], order, child)
+                                            # distribs: 0 block, 1 cyclic, 2 none; darg -1 = default
 
 Workload shapes follow the benchmark configurations: a strided vector of
 float32, the six ghost faces of a 3-D float64 grid, a struct/indexed nest
@@ -77,6 +79,31 @@ def random_spec(rng: np.random.Generator, depth: int = 0, max_depth: int = 3, bi
         st = np.array([rng.integers(0, s - u + 1) for s, u in zip(sizes, sub)], np.int64)
         return ("subarray", sizes.astype(np.int64), sub, st, int(rng.integers(2)), child)
     return ("resized", int(rng.integers(-8, 9)), int(rng.integers(0, 48)), child)
+
+
+def random_darray_spec(rng: np.random.Generator):
+    """A random distributed-array spec over a small global array."""
+    nd = int(rng.integers(1, 4))
+    gs = rng.integers(1, 9, nd).astype(np.int64)
+    ps = np.array([rng.integers(1, 4) for _ in range(nd)], np.int64)
+    dist, dargs = [], []
+    for d in range(nd):
+        kind = int(rng.integers(3))
+        if kind == 2:
+            ps[d] = 1
+        dist.append(kind)
+        if kind == 0:  # block: default, or a block size big enough to cover
+            dargs.append(-1 if rng.random() < 0.5 else int(-(-gs[d] // ps[d]) + rng.integers(0, 3)))
+        elif kind == 1:
+            dargs.append(-1 if rng.random() < 0.5 else int(rng.integers(1, 4)))
+        else:
+            dargs.append(-1)
+    size = int(np.prod(ps))
+    rank = int(rng.integers(size))
+    child = ("basic", str(rng.choice(["int32", "float64", "bfloat16"])))
+    if rng.random() < 0.3:
+        child = ("vector", 2, 1, 2, child)
+    return ("darray", size, rank, gs, dist, np.array(dargs, np.int64), ps, int(rng.integers(2)), child)
 
 
 def sequential_spec(rng: np.random.Generator):

@@ -87,6 +87,16 @@ def test_merging_layouts_pack_unpack():
         check_move(inputs.sequential_spec(rng), int(rng.integers(1, 4)), rng)
 
 
+def test_darray_pack_unpack():
+    rng = np.random.default_rng(204)
+    for _ in range(200):
+        check_move(inputs.random_darray_spec(rng), int(rng.integers(1, 4)), rng)
+    # a 3-D block-cyclic distribution big enough to span many tiles
+    spec = ("darray", 8, 5, [96, 80, 72], [0, 1, 1], [-1, 2, 3], [2, 2, 2], 0, ("basic", "float64"))
+    check_move(spec, 1, rng)
+    check_move(spec[:7] + (1,) + spec[8:], 2, rng)
+
+
 def test_aligned_word_sizes():
     # runs whose lengths and offsets allow 16/8/4/2/1-byte words
     rng = np.random.default_rng(203)

@@ -163,3 +163,29 @@ def test_server_needs_a_device_and_valid_settings():
         with pytest.raises(dte.DteError) as e:
             dte.dte_server_create()
         assert e.value.code in (dte.ERR_NODEVICE, dte.ERR_CUDA)
+
+
+def test_random_darrays_match_oracle():
+    rng = np.random.default_rng(104)
+    for _ in range(400):
+        compare(inputs.random_darray_spec(rng))
+    # darray nested inside other constructors, and other constructors inside it
+    for _ in range(100):
+        d = inputs.random_darray_spec(rng)
+        compare(("contig", 2, d))
+        compare(("darray",) + d[1:8] + (("resized", -4, 12, ("basic", "int32")),))
+
+
+def test_darray_errors():
+    with pytest.raises(dte.DteError) as e:  # block size too small to cover
+        dte.Datatype.darray(2, 0, [9], [dte.DISTRIBUTE_BLOCK], [4], [2], dte.FLOAT64)
+    assert e.value.code == dte.ERR_ARG
+    with pytest.raises(dte.DteError) as e:  # grid of 3 for a size of 4
+        dte.Datatype.darray(4, 0, [8], [dte.DISTRIBUTE_CYCLIC], [dte.DISTRIBUTE_DFLT_DARG], [3], dte.FLOAT64)
+    assert e.value.code == dte.ERR_ARG
+    with pytest.raises(dte.DteError) as e:  # undistributed dimension split over two processes
+        dte.Datatype.darray(2, 0, [8], [dte.DISTRIBUTE_NONE], [dte.DISTRIBUTE_DFLT_DARG], [2], dte.FLOAT64)
+    assert e.value.code == dte.ERR_ARG
+    with pytest.raises(dte.DteError) as e:
+        dte.Datatype.darray(2, 2, [8], [dte.DISTRIBUTE_CYCLIC], [dte.DISTRIBUTE_DFLT_DARG], [2], dte.FLOAT64)
+    assert e.value.code == dte.ERR_ARG

@@ -401,3 +401,72 @@ def test_adjoint_dot_product_and_multiplicity():
     idx = np.repeat(disp, bl) + (np.arange(bl.sum()) - np.repeat(np.cumsum(bl) - bl, bl))
     counts = t.pack_adjoint_f64(np.ones(t.size // 4), 1, n)
     assert np.array_equal(counts, np.bincount(idx, minlength=n).astype(np.float64))
+
+
+def _owned(g, dist, darg, p, c):
+    """Global indices process coordinate c owns along one dimension, from the
+    distribution's definition (block: one contiguous run of b per process;
+    cyclic: blocks of b dealt round-robin; none: everything)."""
+    i = np.arange(g)
+    if dist == o.DIST_NONE:
+        return i
+    if dist == o.DIST_BLOCK:
+        b = -(-g // p) if darg == o.DFLT_DARG else darg
+        return i[(i >= c * b) & (i < (c + 1) * b)]
+    b = 1 if darg == o.DFLT_DARG else darg
+    return i[(i // b) % p == c]
+
+
+def _random_darray(rng):
+    nd = int(rng.integers(1, 4))
+    gs = [int(x) for x in rng.integers(1, 8, nd)]
+    ps, dist, dargs = [], [], []
+    for g in gs:
+        k = int(rng.integers(3))
+        p = 1 if k == o.DIST_NONE else int(rng.integers(1, 4))
+        if k == o.DIST_BLOCK:
+            d = o.DFLT_DARG if rng.random() < 0.5 else -(-g // p) + int(rng.integers(0, 2))
+        elif k == o.DIST_CYCLIC:
+            d = o.DFLT_DARG if rng.random() < 0.5 else int(rng.integers(1, 4))
+        else:
+            d = o.DFLT_DARG
+        ps.append(p), dist.append(k), dargs.append(d)
+    return gs, ps, dist, dargs
+
+
+@pytest.mark.parametrize("order", [o.ORDER_C, o.ORDER_F])
+def test_darray_matches_numpy_ownership(order):
+    """Every rank's darray packs exactly arr[ix_(owned per dim)] in the
+    array's storage order, over a row-major process grid; its extent is the
+    whole global array; and the ranks' typemaps tile the array exactly once."""
+    rng = np.random.default_rng(17 + order)
+    npo = "C" if order == o.ORDER_C else "F"
+    for _ in range(40):
+        gs, ps, dist, dargs = _random_darray(rng)
+        arr = np.asarray(rng.random(tuple(gs)), order=npo)
+        flat = arr.ravel(order="K").view(np.uint8)
+        cover = np.zeros(arr.nbytes, np.int64)
+        size = int(np.prod(ps))
+        for rank in range(size):
+            coords = np.unravel_index(rank, ps)  # process grid is always row-major
+            t = o.darray(size, rank, gs, dist, dargs, ps, F64(), order)
+            idx = [_owned(g, d, a, p, int(c)) for g, d, a, p, c in zip(gs, dist, dargs, ps, coords)]
+            ref = arr[np.ix_(*idx)].ravel(order=npo)
+            assert t.size == ref.nbytes
+            assert (t.lb, t.extent) == (0, arr.nbytes)
+            assert np.array_equal(t.pack(flat, 1).view(np.float64), ref), (gs, ps, dist, dargs, rank)
+            d, sz = t.typemap()
+            for a, s in zip(d, sz):
+                cover[a:a + s] += 1
+        assert np.all(cover == 1)
+
+
+def test_darray_rejects_bad_grids():
+    with pytest.raises(ValueError):  # block too small to cover the dimension
+        o.darray(2, 0, [9], [o.DIST_BLOCK], [4], [2], F64())
+    with pytest.raises(ValueError):  # grid does not have `size` processes
+        o.darray(4, 0, [8], [o.DIST_CYCLIC], [o.DFLT_DARG], [3], F64())
+    with pytest.raises(ValueError):  # undistributed dimension over 2 processes
+        o.darray(2, 0, [8], [o.DIST_NONE], [o.DFLT_DARG], [2], F64())
+    with pytest.raises(ValueError):  # rank out of range
+        o.darray(2, 2, [8], [o.DIST_CYCLIC], [o.DFLT_DARG], [2], F64())
