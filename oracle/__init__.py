@@ -82,6 +82,10 @@ def lib():
         L.or_pack.argtypes = [_p, _i64, _p, _p]
         L.or_pack.restype = C.c_int
         L.or_unpack.argtypes = [_p, _i64, _p, _p]
+        L.or_pack_range.argtypes = [_p, _i64, _p, _i64, _i64, _p]
+        L.or_pack_range.restype = C.c_int
+        L.or_unpack_range.argtypes = [_p, _i64, _i64, _i64, _p, _p]
+        L.or_unpack_range.restype = C.c_int
         L.or_unpack.restype = C.c_int
         L.or_overlaps.argtypes = [_p, _i64]
         L.or_overlaps.restype = C.c_int
@@ -191,6 +195,27 @@ class OType:
         rc = lib().or_unpack(pk.ctypes.data, count, self.h, buf.ctypes.data + base_offset)
         if rc != 0:
             raise ValueError("oracle unpack failed")
+        return origin
+
+    def pack_range(self, origin: np.ndarray, count: int, first: int, nbytes: int,
+                   base_offset: int = 0) -> np.ndarray:
+        """Bytes [first, first + nbytes) of the packed stream of `count` elements."""
+        buf = np.ascontiguousarray(origin).view(np.uint8).reshape(-1)
+        out = np.empty(nbytes, np.uint8)
+        rc = lib().or_pack_range(buf.ctypes.data + base_offset, count, self.h, first, nbytes, out.ctypes.data)
+        if rc != 0:
+            raise ValueError("oracle pack_range: bad argument")
+        return out
+
+    def unpack_range(self, packed: np.ndarray, first: int, count: int, origin: np.ndarray,
+                     base_offset: int = 0):
+        """Unpack packed-stream bytes [first, first + packed.size) into `origin` (in place)."""
+        pk = np.ascontiguousarray(packed).view(np.uint8).reshape(-1)
+        buf = origin.view(np.uint8).reshape(-1)
+        assert buf.flags.c_contiguous
+        rc = lib().or_unpack_range(pk.ctypes.data, first, pk.size, count, self.h, buf.ctypes.data + base_offset)
+        if rc != 0:
+            raise ValueError("oracle unpack_range: bad argument")
         return origin
 
     def overlaps(self, count: int = 1) -> bool:

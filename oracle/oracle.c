@@ -682,6 +682,7 @@ typedef struct {
     unsigned char *dst;
     int64_t pos;
     int to_packed;
+    int64_t lo, hi;  /* packed-stream window moved by the range variants */
 } move_ctx;
 
 static void move_entry(void *vctx, int64_t disp, int64_t size)
@@ -692,6 +693,52 @@ static void move_entry(void *vctx, int64_t disp, int64_t size)
     else
         memcpy(m->dst + disp, m->src + m->pos, (size_t)size);
     m->pos += size;
+}
+
+/* Like move_entry, but only the bytes whose packed-stream position lies in
+ * [lo, hi) move, and packed byte `lo` sits at offset 0 of the packed buffer. */
+static void move_entry_range(void *vctx, int64_t disp, int64_t size)
+{
+    move_ctx *m = (move_ctx *)vctx;
+    int64_t a = m->pos > m->lo ? m->pos : m->lo;
+    int64_t b = m->pos + size < m->hi ? m->pos + size : m->hi;
+    if (a < b) {
+        int64_t ud = disp + (a - m->pos);
+        if (m->to_packed)
+            memcpy(m->dst + (a - m->lo), m->src + ud, (size_t)(b - a));
+        else
+            memcpy(m->dst + ud, m->src + (a - m->lo), (size_t)(b - a));
+    }
+    m->pos += size;
+}
+
+static int move_range(const void *src, void *dst, int to_packed, int64_t count, const or_type *t,
+                      int64_t first, int64_t nbytes)
+{
+    move_ctx m;
+    int64_t e;
+    if (count < 0 || first < 0 || nbytes < 0 || first + nbytes > count * t->size) return OR_EARG;
+    m.src = (const unsigned char *)src;
+    m.dst = (unsigned char *)dst;
+    m.pos = 0;
+    m.to_packed = to_packed;
+    m.lo = first;
+    m.hi = first + nbytes;
+    for (e = 0; e < count && m.pos < m.hi; e++)
+        walk(t, e * ext_of(t), move_entry_range, &m);
+    return OR_OK;
+}
+
+int or_pack_range(const void *origin, int64_t count, const or_type *t, int64_t first, int64_t nbytes,
+                  void *packed)
+{
+    return move_range(origin, packed, 1, count, t, first, nbytes);
+}
+
+int or_unpack_range(const void *packed, int64_t first, int64_t nbytes, int64_t count, const or_type *t,
+                    void *origin)
+{
+    return move_range(packed, origin, 0, count, t, first, nbytes);
 }
 
 int or_pack(const void *origin, int64_t count, const or_type *t, void *packed)

@@ -87,6 +87,14 @@ int64_t or_iov_elements(const or_type *t, int64_t count, int64_t iov_offset,
  * to; `packed` is count*size contiguous bytes. */
 int or_pack(const void *origin, int64_t count, const or_type *t, void *packed);
 int or_unpack(const void *packed, int64_t count, const or_type *t, void *origin);
+/* The same movement restricted to bytes [first, first + nbytes) of the
+ * packed stream of `count` elements; `packed` holds just those bytes.  The
+ * typemap is walked in order and every byte outside the window is skipped,
+ * so a sequence of windows covering the stream equals one full pack. */
+int or_pack_range(const void *origin, int64_t count, const or_type *t, int64_t first, int64_t nbytes,
+                  void *packed);
+int or_unpack_range(const void *packed, int64_t first, int64_t nbytes, int64_t count, const or_type *t,
+                    void *origin);
 /* 1 if two typemap entries of `count` elements share a byte, else 0. */
 int or_overlaps(const or_type *t, int64_t count);
 

@@ -470,3 +470,58 @@ def test_darray_rejects_bad_grids():
         o.darray(2, 0, [8], [o.DIST_NONE], [o.DFLT_DARG], [2], F64())
     with pytest.raises(ValueError):  # rank out of range
         o.darray(2, 2, [8], [o.DIST_CYCLIC], [o.DFLT_DARG], [2], F64())
+
+
+def _stream_addrs(t, count):
+    """User byte address of every packed-stream byte, by expanding the typemap
+    entry by entry (brute force, tiny types only)."""
+    d, s = t.typemap()
+    one = np.concatenate([np.arange(a, a + n) for a, n in zip(d, s)]) if len(d) else np.zeros(0, np.int64)
+    return np.concatenate([one + e * t.extent for e in range(count)]) if count else one[:0]
+
+
+def test_range_moves_follow_the_stream_byte_map():
+    """Range pack / unpack move exactly the packed-stream bytes of the window:
+    brute-force byte maps from the typemap, random windows (ragged, inside one
+    entry, empty, whole stream), and windows that tile the stream reproduce
+    the full pack and unpack."""
+    rng = np.random.default_rng(23)
+    for _ in range(150):
+        t = random_type(rng)
+        count = int(rng.integers(1, 4))
+        addr = _stream_addrs(t, count)
+        total = count * t.size
+        assert addr.size == total
+        if total == 0:
+            continue
+        lo = min(0, int(addr.min()))
+        span = int(addr.max()) - lo + 1
+        src = rng.integers(0, 256, span, dtype=np.uint8)
+        for _ in range(4):
+            a = int(rng.integers(0, total + 1))
+            b = int(rng.integers(a, total + 1))
+            got = t.pack_range(src, count, a, b - a, -lo)
+            assert np.array_equal(got, src[addr[a:b] - lo])
+            win = rng.integers(0, 256, b - a, dtype=np.uint8)
+            dst = np.zeros(span, np.uint8)
+            if not t.overlaps(count):
+                t.unpack_range(win, a, count, dst, -lo)
+                want = np.zeros(span, np.uint8)
+                want[addr[a:b] - lo] = win
+                assert np.array_equal(dst, want)
+        cuts = np.unique(np.concatenate([[0, total], rng.integers(0, total + 1, 5)]))
+        parts = [t.pack_range(src, count, int(x), int(y - x), -lo) for x, y in zip(cuts[:-1], cuts[1:])]
+        full = t.pack(src, count, -lo)
+        assert np.array_equal(np.concatenate(parts), full)
+        if not t.overlaps(count):
+            want = np.zeros(span, np.uint8)
+            t.unpack(full, count, want, -lo)
+            dst = np.zeros(span, np.uint8)
+            order = rng.permutation(len(cuts) - 1)
+            for i in order:
+                x, y = int(cuts[i]), int(cuts[i + 1])
+                t.unpack_range(full[x:y], x, count, dst, -lo)
+            assert np.array_equal(dst, want)
+    t = o.vector(3, 1, 2, F64())
+    with pytest.raises(ValueError):
+        t.pack_range(np.zeros(64, np.uint8), 1, 20, 5)
