@@ -49,10 +49,11 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--config", default="halo",
-                   help="halo (headline, default) | vector | records | batch | largeblock | autograd | all")
+                   help="halo (headline, default) | vector | records | batch | largeblock | autograd | serve | "
+                        "pipeline | all")
     p.add_argument("--records-blocks", type=int, default=1 << 22)
     p.add_argument("--batch-ops", type=int, default=10000)
-    p.add_argument("--serve-requests", type=int, default=1000)
+    p.add_argument("--serve-requests", type=int, default=20000)
     return p.parse_args()
 
 
@@ -719,8 +720,58 @@ def run_config_serve(args):
            "mean_request_bytes_moved": round(float(nbytes.mean()))})
 
 
+def run_config_pipeline(args):
+    """Windowed send-to-self pipeline (pack -> device copy -> unpack per
+    window, one stream): a periodic halo exchange of the 512^3 float64 grid
+    (each of the six 4 MiB send faces into the opposite ghost face) and a
+    256 MiB large-block hvector message, at several staging sizes."""
+    import torch
+    import paper_2402_12274_gb300 as dte
+    from paper_2402_12274_gb300 import inputs
+    dev = torch.device("cuda", 0)
+    s = torch.cuda.Stream()
+    fl = L2Flush(dev)
+    n = 512
+    a = torch.empty(n ** 3, dtype=torch.float64, device=dev)
+    b = torch.empty(n ** 3, dtype=torch.float64, device=dev)
+    send = [dte.Datatype.from_spec(x).commit() for x in inputs.halo_face_specs(n, 2)]
+    recv = [dte.Datatype.from_spec(x).commit() for x in inputs.halo_recv_face_specs(n, 2)]
+    msg = sum(t.size for t in send)
+    halo = {}
+    for st in (256 << 10, 1 << 20, 4 << 20, 16 << 20):
+        g = torch.empty(st, dtype=torch.uint8, device=dev)
+
+        def step():
+            for f in range(6):
+                dte.dte_sendrecv_enqueue(a.data_ptr(), 1, send[f].h, b.data_ptr(), 1, recv[f ^ 1].h,
+                                         g.data_ptr(), st, s.cuda_stream)
+        ts = _mean_s(s, step, 50, fl)
+        halo[f"staging_{st >> 10}KiB"] = {"us": round(ts * 1e6, 1), "message_GBs": round(msg / ts / 1e9, 1),
+                                          "hbm_GBs": round(6 * msg / ts / 1e9, 1)}
+    big = {}
+    L = 65536
+    t = dte.Datatype.hvector((256 << 20) // L, 1, L + L // 2, dte.Datatype.contiguous(L // 8, dte.FLOAT64)).commit()
+    src = torch.empty((256 << 20) * 3 // 2 + (1 << 20), dtype=torch.uint8, device=dev)
+    dst = torch.empty_like(src)
+    for st in (8 << 20, 64 << 20, 512 << 20):
+        g = torch.empty(st, dtype=torch.uint8, device=dev)
+        ts = _mean_s(s, lambda: dte.dte_sendrecv_enqueue(src.data_ptr(), 1, t.h, dst.data_ptr(), 1, t.h,
+                                                         g.data_ptr(), st, s.cuda_stream), 20, fl)
+        big[f"staging_{st >> 20}MiB"] = {"ms": round(ts * 1e3, 3), "message_GBs": round(t.size / ts / 1e9, 1),
+                                         "hbm_GBs": round(6 * t.size / ts / 1e9, 1)}
+    peak, kind = peaks()
+    best = max(v["hbm_GBs"] for v in big.values())
+    _line("send-to-self pipeline: 512^3 f64 periodic halo faces; 256 MiB hvector(64 KiB runs)",
+          "pipeline HBM GB/s (large-block, best staging)", best, "GB/s",
+          {"frac_of_peak": round(best / peak, 4), "peak": peak, "peak_source": kind,
+           "halo_faces": halo, "large_block": big, "halo_message_bytes": msg,
+           "bytes_model": "6 x message (pack r+w, copy r+w, unpack r+w)",
+           "l2": "flushed between reps (write + read 512 MiB)"})
+
+
 CONFIGS = {"vector": run_config_vector, "records": run_config_records, "batch": run_config_batch,
-           "largeblock": run_config_largeblock, "autograd": run_config_autograd, "serve": run_config_serve}
+           "largeblock": run_config_largeblock, "autograd": run_config_autograd, "serve": run_config_serve,
+           "pipeline": run_config_pipeline}
 
 
 def main():

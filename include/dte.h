@@ -254,6 +254,39 @@ DTE_API int dte_pack_enqueue(const void *inbuf, int64_t incount, dte_type type, 
 DTE_API int dte_unpack_enqueue(const void *inbuf, int64_t insize, int64_t *position, void *outbuf,
                        int64_t outcount, dte_type type, dte_stream_t stream);
 
+/* Partial movement: only bytes [first, first + nbytes) of the packed stream
+ * of incount (outcount) elements, i.e. what a full pack would write at those
+ * positions (§3.1: the iov queries address a typemap by packed byte offset).
+ * outbuf (pack) / inbuf (unpack) holds just the nbytes window, packed byte
+ * `first` at offset 0.  A window may start and end anywhere, inside a
+ * segment too; windows that tile [0, count*size) in any order reproduce the
+ * full pack or unpack.  DTE_ERR_ARG for negative arguments or a window past
+ * count*size; DTE_ERR_OVERLAP (unpack) as for dte_unpack_enqueue.  Device
+ * pointers, enqueued on `stream`, no host synchronisation. */
+DTE_API int dte_pack_range_enqueue(const void *inbuf, int64_t incount, dte_type type, int64_t first,
+                                   int64_t nbytes, void *outbuf, dte_stream_t stream);
+DTE_API int dte_unpack_range_enqueue(const void *inbuf, int64_t first, int64_t nbytes, void *outbuf,
+                                     int64_t outcount, dte_type type, dte_stream_t stream);
+
+/* Send-to-self through the enqueue path of §5.2 (MPIX_Send_enqueue paired
+ * with MPIX_Recv_enqueue, here on one GPU and one stream): the message
+ * packed from (sendbuf, sendcount, sendtype) is delivered into (recvbuf,
+ * recvcount, recvtype) -- the first sendcount*size(sendtype) bytes of the
+ * receive stream, the rest of recvbuf untouched.  The message moves in
+ * windows of W = (staging_bytes / 2) rounded down to 16 bytes, each cut at
+ * the last segment boundary of the send layout within W (the byte form of
+ * the iov-length query, §3.1) unless one segment is longer than W; every
+ * window is packed into staging[0, W), copied to staging[W, 2W) (the
+ * transfer) and unpacked from there, in stream order.  `staging` is a
+ * caller-owned device buffer of staging_bytes (>= 32) that must not be used
+ * by other work until the stream passes this call.  DTE_ERR_TRUNCATE if the
+ * receive side holds fewer bytes than the message; DTE_ERR_OVERLAP if the
+ * receive layout writes a byte twice; DTE_ERR_ARG for negative counts, null
+ * pointers or staging_bytes < 32. */
+DTE_API int dte_sendrecv_enqueue(const void *sendbuf, int64_t sendcount, dte_type sendtype, void *recvbuf,
+                                 int64_t recvcount, dte_type recvtype, void *staging, int64_t staging_bytes,
+                                 dte_stream_t stream);
+
 /* Adjoint of a float32 pack (the backward of `packed = pack(x)` in a
  * differentiable solver's halo gather; overlapping layouts are describable,
  * §3): for every packed float k read from float src(k) of the user layout,
@@ -328,7 +361,7 @@ DTE_API int dte_unpack_batch_enqueue(int64_t nops, const dte_op *ops, dte_stream
  * cannot wait on the allocator, libraries handed a stream but not allowed to
  * touch the device heap.  Same result as dte_pack_batch_enqueue.
  *
- * The op table goes into one fixed array of about 43 KB inside the library
+ * The op table goes into one fixed array of about 45 KB inside the library
  * (held on every GPU that loads the library until the process exits)
  * instead of memory from cudaMalloc.  Limits and rules:
  *   - nops <= DTE_NOALLOC_MAX_OPS, else DTE_ERR_UNSUPPORTED (nothing queued);

@@ -104,6 +104,9 @@ _SIGS = {
     "dte_pack_size": ([_i64, _p, _pi64], C.c_int),
     "dte_pack_enqueue": ([_p, _i64, _p, _p, _i64, _pi64, _p], C.c_int),
     "dte_unpack_enqueue": ([_p, _i64, _pi64, _p, _i64, _p, _p], C.c_int),
+    "dte_pack_range_enqueue": ([_p, _i64, _p, _i64, _i64, _p, _p], C.c_int),
+    "dte_unpack_range_enqueue": ([_p, _i64, _i64, _p, _i64, _p, _p], C.c_int),
+    "dte_sendrecv_enqueue": ([_p, _i64, _p, _p, _i64, _p, _p, _i64, _p], C.c_int),
     "dte_batch_create": ([C.c_int, _i64, C.POINTER(dte_op), _pp], C.c_int),
     "dte_batch_set_launch": ([_p, C.c_int, _i64], C.c_int),
     "dte_batch_enqueue": ([_p, _p], C.c_int),
@@ -344,6 +347,23 @@ def dte_unpack_enqueue(inbuf: int, insize: int, position: int, outbuf: int, outc
     _ck(lib.dte_unpack_enqueue(inbuf, insize, C.byref(pos), outbuf, outcount, t, stream),
         "dte_unpack_enqueue")
     return pos.value
+
+
+def dte_pack_range_enqueue(inbuf: int, incount: int, t: int, first: int, nbytes: int, outbuf: int,
+                           stream: int = 0) -> None:
+    _ck(lib.dte_pack_range_enqueue(inbuf, incount, t, first, nbytes, outbuf, stream), "dte_pack_range_enqueue")
+
+
+def dte_unpack_range_enqueue(inbuf: int, first: int, nbytes: int, outbuf: int, outcount: int, t: int,
+                             stream: int = 0) -> None:
+    _ck(lib.dte_unpack_range_enqueue(inbuf, first, nbytes, outbuf, outcount, t, stream),
+        "dte_unpack_range_enqueue")
+
+
+def dte_sendrecv_enqueue(sendbuf: int, sendcount: int, sendtype: int, recvbuf: int, recvcount: int,
+                         recvtype: int, staging: int, staging_bytes: int, stream: int = 0) -> None:
+    _ck(lib.dte_sendrecv_enqueue(sendbuf, sendcount, sendtype, recvbuf, recvcount, recvtype, staging,
+                                 staging_bytes, stream), "dte_sendrecv_enqueue")
 
 
 def _ops_array(ops):
@@ -626,3 +646,38 @@ def unpack(src, position: int, dst, count: int, dtype: Datatype, stream=None, ds
     sp, sn = _ptr_nbytes(src)
     dp, _ = _ptr_nbytes(dst)
     return dte_unpack_enqueue(sp, sn, position, dp + dst_offset, count, dtype.h, _stream_handle(stream))
+
+
+def pack_range(src, count: int, dtype: Datatype, first: int, nbytes: int, dst, stream=None,
+               src_offset: int = 0, dst_offset: int = 0) -> None:
+    """Enqueue packed-stream bytes [first, first + nbytes) of `count` elements
+    (displacement 0 at src + src_offset) into dst + dst_offset."""
+    sp, _ = _ptr_nbytes(src)
+    dp, dn = _ptr_nbytes(dst)
+    if dst_offset < 0 or dst_offset + nbytes > dn:
+        raise ValueError("pack_range: destination too small")
+    dte_pack_range_enqueue(sp + src_offset, count, dtype.h, first, nbytes, dp + dst_offset,
+                           _stream_handle(stream))
+
+
+def unpack_range(src, first: int, nbytes: int, dst, count: int, dtype: Datatype, stream=None,
+                 src_offset: int = 0, dst_offset: int = 0) -> None:
+    """Enqueue the unpack of packed-stream bytes [first, first + nbytes), read
+    from src + src_offset, into `count` elements at dst + dst_offset."""
+    sp, sn = _ptr_nbytes(src)
+    dp, _ = _ptr_nbytes(dst)
+    if src_offset < 0 or src_offset + nbytes > sn:
+        raise ValueError("unpack_range: source too small")
+    dte_unpack_range_enqueue(sp + src_offset, first, nbytes, dp + dst_offset, count, dtype.h,
+                             _stream_handle(stream))
+
+
+def sendrecv(send, sendcount: int, sendtype: Datatype, recv, recvcount: int, recvtype: Datatype, staging,
+             stream=None, send_offset: int = 0, recv_offset: int = 0) -> None:
+    """Enqueue the windowed send-to-self pipeline (pack -> copy -> unpack per
+    window) from `send` to `recv` through the device buffer `staging`."""
+    sp, _ = _ptr_nbytes(send)
+    rp, _ = _ptr_nbytes(recv)
+    gp, gn = _ptr_nbytes(staging)
+    dte_sendrecv_enqueue(sp + send_offset, sendcount, sendtype.h, rp + recv_offset, recvcount, recvtype.h,
+                         gp, gn, _stream_handle(stream))

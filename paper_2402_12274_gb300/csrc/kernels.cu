@@ -70,9 +70,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) move_kernel(Desc d, Op o
 // together: lane l takes words l, l+32, l+64, l+96 of each 128-word slice and
 // finds the segment of each word with a 5-step shuffle search over the
 // lanes' packed start offsets, so packed-side accesses stay coalesced.
+// Segments [seg0, seg0 + nsegs) of the count-level segment list are moved;
+// a range move clips the first and last of them to its packed window.
 template <int W, bool PACK>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) seg_kernel(Desc d, Op op, int64_t nseg_elem, FastDiv div_nseg,
-                                                                  int64_t nsegs, int64_t span)
+                                                                  int64_t seg0, int64_t nsegs, int64_t span)
 {
     extern __shared__ uint4 smem[];
     const char *blob;
@@ -85,7 +87,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) seg_kernel(Desc d, Op op
     for (int64_t s0 = warp * span; s0 < nsegs; s0 += stride) {
         const int64_t s1 = min(s0 + span, nsegs);
         for (int64_t base = s0; base < s1; base += 32)
-            seg_round<W, PACK>(op, nodes, blob, nseg_elem, div_nseg, base, s1, lane, h);
+            seg_round<W, PACK>(op, nodes, blob, nseg_elem, div_nseg, seg0 + base, seg0 + s1, lane, h);
     }
 }
 
@@ -386,6 +388,8 @@ __global__ void __launch_bounds__(kThreads) adjoint_csr_kernel(const int64_t *ro
 // ---------------------------------------------------------------------------
 typedef void (*MoveKernel)(Desc, Op, int64_t, int64_t);
 
+
+
 template <bool PACK>
 static MoveKernel pick_move(int W, bool pk16)
 {
@@ -398,13 +402,27 @@ static MoveKernel pick_move(int W, bool pk16)
     }
 }
 
+// Count-level index of the segment holding packed-stream byte B (< count*size).
+static int64_t segment_of(const Committed &c, int64_t B)
+{
+    int64_t e = B / c.size, k = 0, start = 0;
+    decode_pos(c.nodes(), c.blob(), c.root, B - e * c.size, k, start);
+    return e * c.nseg + k;
+}
+
+// Move packed-stream bytes [first, first + nbytes) of `count` elements
+// (nbytes > 0); `packed` holds just those bytes.  A whole move is
+// first = 0, nbytes = count * size.
 static int launch_move(bool pack, dte_type t, const char *dblob, const void *user, void *packed, int64_t count,
-                       cudaStream_t stream, int dev)
+                       int64_t first, int64_t nbytes, cudaStream_t stream, int dev)
 {
     Committed &c = *t->desc;
     Op op = make_op(c, t->extent(), user, packed, count);
+    op.pbase = first;
+    op.total = nbytes;
     if (op.total == 0) return DTE_SUCCESS;
     int W = word_of(c, t->extent(), count, user, packed);
+    if (first != 0 || nbytes != count * c.size) W = (int)std::min<int64_t>(W, std::min(p2v(first), p2v(nbytes)));
     bool pk16 = p2addr(packed) >= 16;
     MoveKernel k = pack ? pick_move<true>(W, pk16) : pick_move<false>(W, pk16);
     size_t smem = 0;
@@ -418,7 +436,7 @@ static int launch_move(bool pack, dte_type t, const char *dblob, const void *use
     int64_t max_warps = max_blocks * kWarps;
     if (W < 16 && c.maxrun <= kSegMaxRun) {
         // short runs, small words: one decode per segment, cooperative copy
-        typedef void (*SegKernel)(Desc, Op, int64_t, FastDiv, int64_t, int64_t);
+        typedef void (*SegKernel)(Desc, Op, int64_t, FastDiv, int64_t, int64_t, int64_t);
         SegKernel sk;
         switch (W) {
         case 8: sk = pack ? seg_kernel<8, true> : seg_kernel<8, false>; break;
@@ -429,22 +447,23 @@ static int launch_move(bool pack, dte_type t, const char *dblob, const void *use
         static thread_local int socc_cache[64][2][4][3];
         int &socc = socc_cache[dev & 63][pack ? 1 : 0][W == 8 ? 0 : W == 4 ? 1 : W == 2 ? 2 : 3][d.stage];
         if (socc == 0) socc = occupancy(sk, d.stage == STAGE_BLOB ? (size_t)kSmemBlob : smem);
-        int64_t nsegs = count * c.nseg;
+        int64_t seg0 = first == 0 ? 0 : segment_of(c, first);
+        int64_t nsegs = (first + nbytes == count * c.size ? count * c.nseg : segment_of(c, first + nbytes - 1) + 1) - seg0;
         int64_t rounds = (nsegs + 31) / 32;
         int64_t span_rounds = std::max<int64_t>(1, std::min<int64_t>(8, rounds / ((int64_t)sm_count(dev) * socc * kWarps)));
         int64_t units = (rounds + span_rounds - 1) / span_rounds;
         int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((units + kWarps - 1) / kWarps,
                                                                 (int64_t)sm_count(dev) * socc));
-        sk<<<(unsigned)blocks, kThreads, smem, stream>>>(d, op, c.nseg, c.nodes()[c.root].div_nseg, nsegs,
+        sk<<<(unsigned)blocks, kThreads, smem, stream>>>(d, op, c.nseg, c.nodes()[c.root].div_nseg, seg0, nsegs,
                                                         32 * span_rounds);
         if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
         return DTE_SUCCESS;
     }
     int64_t nchunks = (op.total + 15) / 16;
+    int64_t steps = (nchunks + kStep - 1) / kStep;
     // span: one step when the descriptor sits in shared memory; up to eight
     // when index tables are searched in global memory (consecutive steps
     // reuse the search position), but never so many that warps go idle
-    int64_t steps = (nchunks + kStep - 1) / kStep;
     int64_t span_steps = d.stage == STAGE_BLOB ? 1 : std::max<int64_t>(1, std::min<int64_t>(8, steps / max_warps));
     int64_t units = (steps + span_steps - 1) / span_steps;
     int64_t blocks = std::min<int64_t>((units + kWarps - 1) / kWarps, max_blocks);
@@ -559,7 +578,7 @@ int dte_pack_enqueue(const void *inbuf, int64_t incount, dte_type type, void *ou
         const char *blob;
         int dev;
         if (int rc = prep(type, stream, &blob, &dev)) return rc;
-        int rc = launch_move(true, type, blob, inbuf, (char *)outbuf + *position, incount,
+        int rc = launch_move(true, type, blob, inbuf, (char *)outbuf + *position, incount, 0, need,
                              (cudaStream_t)stream, dev);
         if (rc) return rc;
         note_use(type, dev, stream);
@@ -589,11 +608,121 @@ int dte_unpack_enqueue(const void *inbuf, int64_t insize, int64_t *position, voi
         const char *blob;
         int dev;
         if (int rc = prep(type, stream, &blob, &dev)) return rc;
-        int rc = launch_move(false, type, blob, outbuf, (char *)inbuf + *position, outcount,
+        int rc = launch_move(false, type, blob, outbuf, (char *)inbuf + *position, outcount, 0, need,
                              (cudaStream_t)stream, dev);
         if (rc) return rc;
         note_use(type, dev, stream);
         *position += need;
+        return DTE_SUCCESS;
+    } catch (const Error &e) {
+        return e.code;
+    } catch (...) {
+        return DTE_ERR_NOMEM;
+    }
+}
+
+int dte_pack_range_enqueue(const void *inbuf, int64_t incount, dte_type type, int64_t first, int64_t nbytes,
+                           void *outbuf, dte_stream_t stream)
+{
+    try {
+        if (!handle_valid(type)) return DTE_ERR_TYPE;
+        if (!type->committed) return DTE_ERR_TYPE;
+        if (incount < 0 || first < 0 || nbytes < 0) return DTE_ERR_ARG;
+        int64_t total, end;
+        if (__builtin_mul_overflow(incount, type->size, &total)) return DTE_ERR_OVERFLOW;
+        if (__builtin_add_overflow(first, nbytes, &end) || end > total) return DTE_ERR_ARG;
+        if (nbytes == 0) return DTE_SUCCESS;
+        if (!inbuf || !outbuf) return DTE_ERR_ARG;
+        const char *blob;
+        int dev;
+        if (int rc = prep(type, stream, &blob, &dev)) return rc;
+        if (int rc = launch_move(true, type, blob, inbuf, outbuf, incount, first, nbytes, (cudaStream_t)stream, dev))
+            return rc;
+        note_use(type, dev, stream);
+        return DTE_SUCCESS;
+    } catch (const Error &e) {
+        return e.code;
+    } catch (...) {
+        return DTE_ERR_NOMEM;
+    }
+}
+
+int dte_unpack_range_enqueue(const void *inbuf, int64_t first, int64_t nbytes, void *outbuf, int64_t outcount,
+                             dte_type type, dte_stream_t stream)
+{
+    try {
+        if (!handle_valid(type)) return DTE_ERR_TYPE;
+        if (!type->committed) return DTE_ERR_TYPE;
+        if (outcount < 0 || first < 0 || nbytes < 0) return DTE_ERR_ARG;
+        int64_t total, end;
+        if (__builtin_mul_overflow(outcount, type->size, &total)) return DTE_ERR_OVERFLOW;
+        if (__builtin_add_overflow(first, nbytes, &end) || end > total) return DTE_ERR_ARG;
+        if (nbytes == 0) return DTE_SUCCESS;
+        if (!inbuf || !outbuf) return DTE_ERR_ARG;
+        if (committed_overlaps(*type->desc, outcount, type->extent())) return DTE_ERR_OVERLAP;
+        const char *blob;
+        int dev;
+        if (int rc = prep(type, stream, &blob, &dev)) return rc;
+        if (int rc = launch_move(false, type, blob, outbuf, const_cast<void *>(inbuf), outcount, first, nbytes,
+                                 (cudaStream_t)stream, dev))
+            return rc;
+        note_use(type, dev, stream);
+        return DTE_SUCCESS;
+    } catch (const Error &e) {
+        return e.code;
+    } catch (...) {
+        return DTE_ERR_NOMEM;
+    }
+}
+
+// Send-to-self pipeline (§5.2's enqueued send and receive on one stream):
+// the message is cut into windows that end on segment boundaries of the send
+// layout (the byte-window form of the iov-length query, §3.1) unless a
+// single segment is longer than the window; each window is packed into the
+// sender half of `staging`, copied to the receiver half (the transfer), and
+// unpacked from there, all in stream order.
+int dte_sendrecv_enqueue(const void *sendbuf, int64_t sendcount, dte_type sendtype, void *recvbuf,
+                         int64_t recvcount, dte_type recvtype, void *staging, int64_t staging_bytes,
+                         dte_stream_t stream)
+{
+    try {
+        if (!handle_valid(sendtype) || !handle_valid(recvtype)) return DTE_ERR_TYPE;
+        if (!sendtype->committed || !recvtype->committed) return DTE_ERR_TYPE;
+        if (sendcount < 0 || recvcount < 0 || staging_bytes < 0) return DTE_ERR_ARG;
+        int64_t S, R;
+        if (__builtin_mul_overflow(sendcount, sendtype->size, &S) ||
+            __builtin_mul_overflow(recvcount, recvtype->size, &R))
+            return DTE_ERR_OVERFLOW;
+        if (S > R) return DTE_ERR_TRUNCATE;
+        if (S == 0) return DTE_SUCCESS;
+        const int64_t window = (staging_bytes / 2) & ~(int64_t)15;
+        if (!sendbuf || !recvbuf || !staging || window <= 0) return DTE_ERR_ARG;
+        if (committed_overlaps(*recvtype->desc, recvcount, recvtype->extent())) return DTE_ERR_OVERLAP;
+        const char *sblob, *rblob;
+        int dev, rdev;
+        if (int rc = prep(sendtype, stream, &sblob, &dev)) return rc;
+        if (int rc = prep(recvtype, stream, &rblob, &rdev)) return rc;
+        char *tx = (char *)staging, *rx = (char *)staging + window;
+        const Committed &sc = *sendtype->desc;
+        const cudaStream_t st = (cudaStream_t)stream;
+        for (int64_t off = 0; off < S;) {
+            int64_t end = std::min(S, off + window);
+            if (end < S) {
+                int64_t e = end / sc.size, k = 0, start = 0;
+                decode_pos(sc.nodes(), sc.blob(), sc.root, end - e * sc.size, k, start);
+                if (e * sc.size + start > off) end = e * sc.size + start;
+            }
+            const int64_t n = end - off;
+            if (int rc = launch_move(true, sendtype, sblob, sendbuf, tx, sendcount, off, n, st, dev)) return rc;
+            if (cudaMemcpyAsync(rx, tx, (size_t)n, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+                cudaGetLastError();
+                return DTE_ERR_CUDA;
+            }
+            if (int rc = launch_move(false, recvtype, rblob, recvbuf, rx, recvcount, off, n, st, rdev)) return rc;
+            off = end;
+        }
+        note_use(sendtype, dev, stream);
+        note_use(recvtype, rdev, stream);
         return DTE_SUCCESS;
     } catch (const Error &e) {
         return e.code;

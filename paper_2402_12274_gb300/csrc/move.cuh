@@ -49,6 +49,7 @@ struct Op {
     const char *packed_in;  // unpack source (position applied)
     char *packed_out;       // pack destination (position applied)
     int64_t total;          // bytes moved
+    int64_t pbase;          // packed-stream offset of packed byte 0 (range moves; else 0)
     int64_t esize;          // element size
     int64_t extent;         // element stride
     FastDiv ediv;           // / esize
@@ -93,10 +94,12 @@ union Chunk {
     typename Word<W>::T w[16 / W];
 };
 
-// packed offset P -> user displacement and bytes left in that run
+// packed offset P (of this op's packed buffer) -> user displacement and
+// bytes left in that run
 __device__ __forceinline__ void locate(const Op &op, const DNode *nodes, const char *blob, int64_t P,
                                        int64_t &d, int64_t &rem, Hint &h)
 {
+    P += op.pbase;
     int64_t e = fdiv(P, op.ediv);
     d = e * op.extent;
     decode_bytes(nodes, blob, op.root, P - e * op.esize, d, rem, h);
@@ -279,9 +282,13 @@ __device__ __forceinline__ void seg_round(const Op &op, const DNode *nodes, cons
         decode_seg(nodes, blob, op.root, k - e * nseg_elem, disp, len, ps, h);
         ps += e * op.esize;
     }
-    const int64_t p0 = __shfl_sync(FULL, ps, 0);
-    const int64_t p1 = __shfl_sync(FULL, ps + len, nvalid - 1);
+    // packed-stream range of the 32 segments, clipped to the op's window
+    // (a range move may start or end inside a segment)
+    const int64_t p0 = max(__shfl_sync(FULL, ps, 0), op.pbase);
+    const int64_t p1 = min(__shfl_sync(FULL, ps + len, nvalid - 1), op.pbase + op.total);
     const int64_t nwords = (p1 - p0) / W;
+    const char *pk_in = op.packed_in - op.pbase;  // indexed by stream offset
+    char *pk_out = op.packed_out - op.pbase;
     for (int64_t w0 = 0; w0 < nwords; w0 += 32 * kU) {
         T v[kU];
         int64_t ud[kU];
@@ -299,14 +306,14 @@ __device__ __forceinline__ void seg_round(const Op &op, const DNode *nodes, cons
             ud[u] = __shfl_sync(FULL, disp, lo) + (q - __shfl_sync(FULL, ps, lo));
             if (wi < nwords) {
                 if (PACK) v[u] = ldw<W>(op.user_in + ud[u]);
-                else v[u] = ldw<W>(op.packed_in + q);
+                else v[u] = ldw<W>(pk_in + q);
             }
         }
 #pragma unroll
         for (int u = 0; u < kU; u++) {
             const int64_t wi = w0 + u * 32 + lane;
             if (wi < nwords) {
-                if (PACK) stw<W>(op.packed_out + p0 + wi * W, v[u]);
+                if (PACK) stw<W>(pk_out + p0 + wi * W, v[u]);
                 else stw<W>(op.user_out + ud[u], v[u]);
             }
         }
@@ -422,6 +429,7 @@ static Op make_op(const Committed &c, int64_t extent, const void *user, void *pa
     op.packed_in = (const char *)packed;
     op.packed_out = (char *)packed;
     op.total = count * c.size;
+    op.pbase = 0;
     op.esize = c.size;
     op.extent = extent;
     op.ediv = c.nodes()[c.root].div_size;

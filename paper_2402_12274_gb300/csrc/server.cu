@@ -10,10 +10,12 @@
 //
 //   host                                   device (persistent kernel)
 //   ----                                   ---------------------------
-//   submit -> FIFO; admit while ring       warps claim tiles of the oldest
-//   slots and the byte cap allow: write    published request with a CAS on a
-//   the record, then publish (release)     (request, tile) cursor -- never more
-//                                          than is published -- and move them
+//   submit -> FIFO; admit while ring       warps walk the published requests
+//   slots and the byte cap allow: write    in order and claim tiles with a
+//   the record, then publish (release)     fetch-add on the slot's counter,
+//                                          tagged with the request number so a
+//                                          reused slot is never confused; the
+//                                          record is mirrored into device memory
 //   progress: read completion words        the last warp of a request writes its
 //   (acquire), free capacity, admit more   completion word (release, system scope)
 //

@@ -19,3 +19,13 @@ def iov_arrays(t, offset=0, max_len=None):
     d = np.array([a for a, _ in lst], np.int64)
     l = np.array([b for _, b in lst], np.int64)
     return d, l
+
+
+def span_of(o, count):
+    """(lo, hi) byte range touched by `count` elements, relative to displacement 0."""
+    if o.size == 0 or count == 0:
+        return 0, 0
+    ends = [e * o.extent for e in (0, count - 1)]
+    lo = min(e + o.true_lb for e in ends)
+    hi = max(e + o.true_lb + o.true_extent for e in ends)
+    return lo, hi

@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 from paper_2402_12274_gb300 import inputs
-from tests.helpers import both
+from tests.helpers import both, span_of
 
 torch = pytest.importorskip("torch")
 import paper_2402_12274_gb300 as dte  # noqa: E402
@@ -15,16 +15,6 @@ import paper_2402_12274_gb300 as dte  # noqa: E402
 pytestmark = pytest.mark.gpu
 DEV = "cuda"
 SENT = 0xA5
-
-
-def span_of(o, count):
-    """(lo, hi) byte range touched by `count` elements, relative to displacement 0."""
-    if o.size == 0 or count == 0:
-        return 0, 0
-    ends = [e * o.extent for e in (0, count - 1)]
-    lo = min(e + o.true_lb for e in ends)
-    hi = max(e + o.true_lb + o.true_extent for e in ends)
-    return lo, hi
 
 
 def gpu_pack(t, src_np, count, base, pk_pos=0, stream=None):

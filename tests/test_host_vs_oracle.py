@@ -189,3 +189,28 @@ def test_darray_errors():
     with pytest.raises(dte.DteError) as e:
         dte.Datatype.darray(2, 2, [8], [dte.DISTRIBUTE_CYCLIC], [dte.DISTRIBUTE_DFLT_DARG], [2], dte.FLOAT64)
     assert e.value.code == dte.ERR_ARG
+
+
+def test_range_and_sendrecv_argument_checks():
+    # these checks run before any device work, so they hold without a GPU
+    t = dte.Datatype.vector(10, 1, 2, dte.FLOAT32).commit()
+    u = dte.Datatype.contiguous(5, dte.FLOAT32).commit()
+    for first, n in ((-1, 4), (0, -4), (30, 11), (41, 0)):
+        with pytest.raises(dte.DteError) as e:
+            dte.dte_pack_range_enqueue(16, 1, t.h, first, n, 16)
+        assert e.value.code == dte.ERR_ARG
+        with pytest.raises(dte.DteError) as e:
+            dte.dte_unpack_range_enqueue(16, first, n, 16, 1, t.h)
+        assert e.value.code == dte.ERR_ARG
+    dte.dte_pack_range_enqueue(16, 1, t.h, 40, 0, 16)  # empty window at the end: nothing to do
+    with pytest.raises(dte.DteError) as e:  # 40-byte message into a 20-byte receive
+        dte.dte_sendrecv_enqueue(16, 1, t.h, 16, 1, u.h, 16, 64)
+    assert e.value.code == dte.ERR_TRUNCATE
+    with pytest.raises(dte.DteError) as e:
+        dte.dte_sendrecv_enqueue(16, 1, u.h, 16, 2, t.h, 16, -1)
+    assert e.value.code == dte.ERR_ARG
+    v = dte.Datatype.vector(3, 1, 2, dte.FLOAT32)  # not committed
+    with pytest.raises(dte.DteError) as e:
+        dte.dte_sendrecv_enqueue(16, 1, v.h, 16, 1, u.h, 16, 64)
+    assert e.value.code == dte.ERR_TYPE
+    dte.dte_sendrecv_enqueue(16, 0, u.h, 16, 0, t.h, 16, 64)  # empty message
