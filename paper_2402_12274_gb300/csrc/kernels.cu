@@ -40,11 +40,13 @@
 
 namespace dte {
 
-// Warps take spans of `span` chunks (a multiple of kStep) round-robin, so
-// every warp sees every part of the layout (costly and cheap regions mix)
-// while a span keeps consecutive steps together for the search hints.
+// Warps take spans of `span` chunks (a multiple of kStep) in the spread
+// order (see Spread), so costly and cheap regions of a layout are worked on
+// at the same time, while a span keeps consecutive steps together for the
+// search hints.
 template <int W, bool PACK, bool PK16>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) move_kernel(Desc d, Op op, int64_t nchunks, int64_t span)
+__global__ void __launch_bounds__(kThreads, kMinBlocks) move_kernel(Desc d, Op op, int64_t nchunks, int64_t span,
+                                                                   Spread sp)
 {
     extern __shared__ uint4 smem[];
     const char *blob;
@@ -52,14 +54,16 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) move_kernel(Desc d, Op o
     stage_desc(d, smem, blob, nodes);
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
-    const int64_t stride = (int64_t)gridDim.x * kWarps * span;
-    Hint h[kU];
-#pragma unroll
-    for (int u = 0; u < kU; u++) h[u] = Hint{-1, 0};
-    for (int64_t c0 = warp * span; c0 < nchunks; c0 += stride) {
+    const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+    Hint h{-1, 0};
+    int64_t p = warp < sp.nspans ? (warp * sp.mult) % sp.nspans : 0;
+    for (int64_t j = warp; j < sp.nspans; j += nwarps) {
+        const int64_t c0 = p * span;
         const int64_t c1 = min(c0 + span, nchunks);
         for (int64_t base = c0; base < c1; base += kStep)
             warp_step<W, PACK, PK16>(op, nodes, blob, base, c1, lane, h);
+        p += sp.inc;
+        if (p >= sp.nspans) p -= sp.nspans;
     }
 }
 
@@ -97,15 +101,17 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) seg_kernel(Desc d, Op op
 // One launch per copy-word class present in a batch: ops are grouped by
 // (W, packed side 16-aligned) so each kernel is specialised like move_kernel.
 // tile0: nops+1 prefix of 2 KiB tiles per op of the group.  Warps take spans
-// of `span` consecutive tiles round-robin.  When the group's descriptors fit
+// of `span` consecutive tiles in the spread order.  When the group's descriptors fit
 // in shared memory together (`image`, image_bytes > 0) they are staged once
 // per CTA and every op with soff >= 0 walks its staged copy.
 template <int W, bool PACK, bool PK16>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_kernel(const BatchOp *ops, const int64_t *tile0, int64_t nops,
                                                          int64_t ntiles, int64_t span, const char *image,
-                                                         int64_t image_bytes)
+                                                         int64_t image_bytes, Spread sp)
 {
     extern __shared__ uint4 smem[];
+    __shared__ Op wop[kWarps];  // the op each warp is working on
+    const int wid = threadIdx.x >> 5;
     if (image_bytes > 0) {
         const uint4 *s = reinterpret_cast<const uint4 *>(image);
         int nw = (int)(image_bytes / 16);
@@ -114,25 +120,27 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_kernel(const Batch
     }
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
-    const int64_t stride = (int64_t)gridDim.x * kWarps * span;
+    const int64_t nwarps = (int64_t)gridDim.x * kWarps;
     Hint oh{-1, 0};
-    Hint h[kU];
+    Hint h{-1, 0};
     int64_t cur = -1;
-    for (int64_t s0 = warp * span; s0 < ntiles; s0 += stride) {
+    int64_t p = warp < sp.nspans ? (warp * sp.mult) % sp.nspans : 0;
+    for (int64_t j = warp; j < sp.nspans; j += nwarps, p = p + sp.inc >= sp.nspans ? p + sp.inc - sp.nspans : p + sp.inc) {
+        const int64_t s0 = p * span;
         const int64_t s1 = min(s0 + span, ntiles);
         for (int64_t t = s0; t < s1; t++) {
             int64_t i = find_le(tile0, nops, t, oh, 0);
-            if (i != cur) {
-#pragma unroll
-                for (int u = 0; u < kU; u++) h[u] = Hint{-1, 0};
-                cur = i;
-            }
             const BatchOp *b = ops + i;
+            if (i != cur) {
+                h = Hint{-1, 0};
+                cur = i;
+                load_op(wop[wid], b->op, lane);
+            }
             const int soff = b->soff;
             const char *blob = soff >= 0 ? reinterpret_cast<const char *>(smem) + soff : b->d.blob;
             const DNode *nodes = reinterpret_cast<const DNode *>(blob + sizeof(BlobHeader));
             int64_t base = (t - tile0[i]) * kStep;
-            warp_step<W, PACK, PK16>(b->op, nodes, blob, base, b->nchunks, lane, h);
+            warp_step<W, PACK, PK16>(wop[wid], nodes, blob, base, b->nchunks, lane, h);
         }
     }
 }
@@ -142,9 +150,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_kernel(const Batch
 template <int W, bool PACK>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_seg_kernel(const BatchOp *ops, const int64_t *tile0,
                                                                         int64_t nops, int64_t ntiles, int64_t span,
-                                                                        const char *image, int64_t image_bytes)
+                                                                        const char *image, int64_t image_bytes,
+                                                                        Spread sp)
 {
     extern __shared__ uint4 smem[];
+    __shared__ Op wop[kWarps];  // the op each warp is working on
+    const int wid = threadIdx.x >> 5;
     if (image_bytes > 0) {
         const uint4 *s = reinterpret_cast<const uint4 *>(image);
         int nw = (int)(image_bytes / 16);
@@ -153,29 +164,33 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_seg_kernel(const B
     }
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
-    const int64_t stride = (int64_t)gridDim.x * kWarps * span;
+    const int64_t nwarps = (int64_t)gridDim.x * kWarps;
     Hint oh{-1, 0};
     Hint h{-1, 0};
     int64_t cur = -1;
-    for (int64_t s0 = warp * span; s0 < ntiles; s0 += stride) {
+    int64_t p = warp < sp.nspans ? (warp * sp.mult) % sp.nspans : 0;
+    for (int64_t j = warp; j < sp.nspans; j += nwarps, p = p + sp.inc >= sp.nspans ? p + sp.inc - sp.nspans : p + sp.inc) {
+        const int64_t s0 = p * span;
         const int64_t s1 = min(s0 + span, ntiles);
         for (int64_t t = s0; t < s1; t++) {
             int64_t i = find_le(tile0, nops, t, oh, 0);
+            const BatchOp *b = ops + i;
             if (i != cur) {
                 h = Hint{-1, 0};
                 cur = i;
+                load_op(wop[wid], b->op, lane);
             }
-            const BatchOp *b = ops + i;
             const int soff = b->soff;
             const char *blob = soff >= 0 ? reinterpret_cast<const char *>(smem) + soff : b->d.blob;
             const DNode *nodes = reinterpret_cast<const DNode *>(blob + sizeof(BlobHeader));
             const int64_t base = (t - tile0[i]) * 32;
-            seg_round<W, PACK>(b->op, nodes, blob, b->nseg_elem, b->div_nseg, base, b->nsegs, lane, h);
+            seg_round<W, PACK>(wop[wid], nodes, blob, b->nseg_elem, b->div_nseg, base, b->nsegs, lane, h);
         }
     }
 }
 
-typedef void (*BatchKernel)(const BatchOp *, const int64_t *, int64_t, int64_t, int64_t, const char *, int64_t);
+typedef void (*BatchKernel)(const BatchOp *, const int64_t *, int64_t, int64_t, int64_t, const char *, int64_t,
+                            Spread);
 
 template <bool PACK>
 static BatchKernel pick_batch(int wsel)
@@ -328,9 +343,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) adjoint_kernel(Desc d, O
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int64_t stride = (int64_t)gridDim.x * kWarps * span;
-    Hint h[kU];
-#pragma unroll
-    for (int u = 0; u < kU; u++) h[u] = Hint{-1, 0};
+    Hint h{-1, 0};
     for (int64_t c0 = warp * span; c0 < nchunks; c0 += stride) {
         const int64_t c1 = min(c0 + span, nchunks);
         for (int64_t base = c0; base < c1; base += kStep) {
@@ -355,7 +368,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) adjoint_kernel(Desc d, O
 #pragma unroll
                     for (int s = 0; s < 4; s++) {
                         if (s * 4 < nb) {
-                            if (rem <= 0) locate(op, nodes, blob, P + s * 4, dd, rem, h[u]);
+                            if (rem <= 0) locate(op, nodes, blob, P + s * 4, dd, rem, h);
                             float *p = reinterpret_cast<float *>(op.user_out + dd);
                             *p = *p + __uint_as_float(ch.w[s]);
                             dd += 4;
@@ -386,7 +399,7 @@ __global__ void __launch_bounds__(kThreads) adjoint_csr_kernel(const int64_t *ro
 // ---------------------------------------------------------------------------
 // launch helpers
 // ---------------------------------------------------------------------------
-typedef void (*MoveKernel)(Desc, Op, int64_t, int64_t);
+typedef void (*MoveKernel)(Desc, Op, int64_t, int64_t, Spread);
 
 
 
@@ -468,7 +481,8 @@ static int launch_move(bool pack, dte_type t, const char *dblob, const void *use
     int64_t units = (steps + span_steps - 1) / span_steps;
     int64_t blocks = std::min<int64_t>((units + kWarps - 1) / kWarps, max_blocks);
     if (blocks < 1) blocks = 1;
-    k<<<(unsigned)blocks, kThreads, smem, stream>>>(d, op, nchunks, span_steps * kStep);
+    k<<<(unsigned)blocks, kThreads, smem, stream>>>(d, op, nchunks, span_steps * kStep,
+                                                    make_spread(units, blocks * kWarps));
     if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
     return DTE_SUCCESS;
 }
@@ -884,7 +898,8 @@ int dte_batch_enqueue(dte_batch b, dte_stream_t stream)
         int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((units + kWarps - 1) / kWarps, max_blocks));
         BatchKernel k = b->kind == DTE_BATCH_PACK ? pick_batch<true>(g.wsel) : pick_batch<false>(g.wsel);
         k<<<(unsigned)blocks, kThreads, (size_t)g.image_bytes, (cudaStream_t)stream>>>(
-            b->d_ops + g.op0, b->d_tile0 + g.t0, g.nops, g.ntiles, span, b->d_image + g.image_off, g.image_bytes);
+            b->d_ops + g.op0, b->d_tile0 + g.t0, g.nops, g.ntiles, span, b->d_image + g.image_off, g.image_bytes,
+            make_spread(units, blocks * kWarps));
         if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
     }
     if (capturing(stream)) {
@@ -1183,7 +1198,8 @@ extern "C" int dte_pack_batch_enqueue_noalloc(int64_t nops, const dte_op *ops, d
             int64_t max_blocks = (int64_t)sm_count(dev) * occ;
             int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((g.ntiles + kWarps - 1) / kWarps, max_blocks));
             k<<<(unsigned)blocks, kThreads, 0, (cudaStream_t)stream>>>(d_ops + g.op0, d_prefix + g.t0, g.nops,
-                                                                      g.ntiles, 1, nullptr, 0);
+                                                                      g.ntiles, 1, nullptr, 0,
+                                                                      make_spread(g.ntiles, blocks * kWarps));
             if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
         }
         return DTE_SUCCESS;

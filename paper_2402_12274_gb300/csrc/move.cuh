@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <numeric>
 
 #include "internal.h"
 
@@ -93,6 +94,30 @@ union Chunk {
     uint4 v;
     typename Word<W>::T w[16 / W];
 };
+
+// Order in which warps visit spans.  The j-th span a launch hands out
+// (j = warp, warp + nwarps, ...) is span (j * mult) mod nspans, with mult
+// coprime to nspans (a bijection) and close to nspans / phi: the spans in
+// flight at any moment are spread over the whole packed range, so regions
+// of a layout that are slow per byte (short runs far apart) run side by side
+// with fast ones instead of being left to the end of the launch.
+struct Spread {
+    int64_t nspans;
+    int64_t mult;
+    int64_t inc;  // (nwarps * mult) mod nspans
+};
+
+// Copy an op record (global) into the warp's shared slot; the kernels that
+// walk many ops read the fields from there instead of holding them in
+// registers.  Synchronised on both sides within the warp.
+__device__ __forceinline__ void load_op(Op &dst, const Op &src, int lane)
+{
+    static_assert(sizeof(Op) % 8 == 0 && sizeof(Op) / 8 <= 32, "Op is copied one word per lane");
+    __syncwarp();
+    if (lane < (int)(sizeof(Op) / 8))
+        reinterpret_cast<unsigned long long *>(&dst)[lane] = reinterpret_cast<const unsigned long long *>(&src)[lane];
+    __syncwarp();
+}
 
 // packed offset P (of this op's packed buffer) -> user displacement and
 // bytes left in that run
@@ -198,7 +223,7 @@ __device__ __forceinline__ void store_packed(char *p, uint4 v, int nb)
 // user address follows without walking the descriptor again.
 template <bool PACK>
 __device__ __forceinline__ void warp_step16(const Op &op, const DNode *nodes, const char *blob, int64_t base,
-                                            int64_t end, int lane, Hint *h)
+                                            int64_t end, int lane, Hint &h)
 {
     uint4 v[kU];
     int64_t d[kU];
@@ -211,7 +236,7 @@ __device__ __forceinline__ void warp_step16(const Op &op, const DNode *nodes, co
                 d[u] = d0 + u * 512;
             } else {
                 int64_t rem;
-                locate(op, nodes, blob, c * 16, d[u], rem, h[u]);
+                locate(op, nodes, blob, c * 16, d[u], rem, h);
                 if (u == 0) {
                     d0 = d[u];
                     rem0 = rem;
@@ -234,7 +259,7 @@ __device__ __forceinline__ void warp_step16(const Op &op, const DNode *nodes, co
 // One warp step: chunks [base, base + kStep) clipped to `end`.
 template <int W, bool PACK, bool PK16>
 __device__ __forceinline__ void warp_step(const Op &op, const DNode *nodes, const char *blob, int64_t base,
-                                          int64_t end, int lane, Hint *h)
+                                          int64_t end, int lane, Hint &h)
 {
     if (W == 16) {
         warp_step16<PACK>(op, nodes, blob, base, end, lane, h);
@@ -247,7 +272,7 @@ __device__ __forceinline__ void warp_step(const Op &op, const DNode *nodes, cons
         if (c < end) {
             int64_t P = c * 16;
             int nb = (int)(op.total - P < 16 ? op.total - P : 16);
-            if (PACK) v[u] = gather_chunk<W>(op, nodes, blob, P, nb, h[u]);
+            if (PACK) v[u] = gather_chunk<W>(op, nodes, blob, P, nb, h);
             else v[u] = load_packed<W, PK16>(op.packed_in + P, nb);
         }
     }
@@ -258,7 +283,7 @@ __device__ __forceinline__ void warp_step(const Op &op, const DNode *nodes, cons
             int64_t P = c * 16;
             int nb = (int)(op.total - P < 16 ? op.total - P : 16);
             if (PACK) store_packed<W, PK16>(op.packed_out + P, v[u], nb);
-            else scatter_chunk<W>(op, nodes, blob, P, nb, v[u], h[u]);
+            else scatter_chunk<W>(op, nodes, blob, P, nb, v[u], h);
         }
     }
 }
@@ -436,6 +461,21 @@ static Op make_op(const Committed &c, int64_t extent, const void *user, void *pa
     op.root = c.root;
     op.pad_ = 0;
     return op;
+}
+
+static Spread make_spread(int64_t nspans, int64_t nwarps)
+{
+    Spread sp;
+    sp.nspans = nspans;
+    sp.mult = 1;
+    if (nspans > 2) {
+        int64_t m = (int64_t)((double)nspans * 0.6180339887498949);
+        if (m < 1) m = 1;
+        while (std::gcd(m, nspans) != 1) m++;
+        sp.mult = m;
+    }
+    sp.inc = nspans > 0 ? (int64_t)(((__int128)nwarps * sp.mult) % nspans) : 0;
+    return sp;
 }
 
 static bool capturing(dte_stream_t stream)
