@@ -50,7 +50,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--config", default="halo",
                    help="halo (headline, default) | vector | records | batch | largeblock | autograd | serve | "
-                        "pipeline | all")
+                        "pipeline | faces | all")
     p.add_argument("--records-blocks", type=int, default=1 << 22)
     p.add_argument("--batch-ops", type=int, default=10000)
     p.add_argument("--serve-requests", type=int, default=20000)
@@ -769,9 +769,61 @@ def run_config_pipeline(args):
            "l2": "flushed between reps (write + read 512 MiB)"})
 
 
+def run_config_faces(args):
+    """Breakdown of the headline halo step: each of the six faces of the
+    512^3 float64 grid packed and unpacked alone, the same face moved by a
+    torch strided copy, and the unpack batch split into the faces with long
+    runs and the two faces normal to the fastest axis (16-byte runs)."""
+    import torch
+    import paper_2402_12274_gb300 as dte
+    from paper_2402_12274_gb300 import inputs
+    dev = torch.device("cuda", 0)
+    s = torch.cuda.Stream()
+    fl = L2Flush(dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(2)
+    grid = torch.randn(N ** 3, dtype=torch.float64, device=dev, generator=gen)
+    grid2 = torch.zeros_like(grid)
+    specs = inputs.halo_face_specs(N, G)
+    faces = [dte.Datatype.from_spec(f).commit() for f in specs]
+    g3, h3 = grid.view(N, N, N), grid2.view(N, N, N)
+    R = 100
+    res = {}
+    for i, (f, sp) in enumerate(zip(faces, specs)):
+        pk = torch.empty(f.size, dtype=torch.uint8, device=dev)
+        sl = tuple(slice(int(a), int(a + b)) for a, b in zip(sp[3], sp[2]))
+        pv = pk.view(torch.float64).view(tuple(int(x) for x in sp[2]))
+        tp = _mean_s(s, lambda: dte.dte_pack_enqueue(grid.data_ptr(), 1, f.h, pk.data_ptr(), f.size, 0,
+                                                     s.cuda_stream), R, fl)
+        tu = _mean_s(s, lambda: dte.dte_unpack_enqueue(pk.data_ptr(), f.size, 0, grid2.data_ptr(), 1, f.h,
+                                                       s.cuda_stream), R, fl)
+        ttp = _mean_s(s, lambda: pv.copy_(g3[sl]), R, fl)
+        ttu = _mean_s(s, lambda: h3[sl].copy_(pv), R, fl)
+        res[f"face{i}_axis{i // 2}"] = {"pack_us": round(tp * 1e6, 2), "unpack_us": round(tu * 1e6, 2),
+                                        "torch_copy_in_us": round(ttp * 1e6, 2),
+                                        "torch_copy_out_us": round(ttu * 1e6, 2)}
+    offs = np.concatenate([[0], np.cumsum([f.size for f in faces])[:-1]]).tolist()
+    packed = torch.empty(sum(f.size for f in faces), dtype=torch.uint8, device=dev)
+    send = dte.Datatype.from_spec(inputs.all_faces_struct(specs)).commit()
+    t_pack = _mean_s(s, lambda: dte.dte_pack_enqueue(grid.data_ptr(), 1, send.h, packed.data_ptr(), send.size, 0,
+                                                     s.cuda_stream), R, fl)
+    parts = {}
+    for name, idx in (("all_six", range(6)), ("axes_0_1", [0, 1, 2, 3]), ("axis_2", [4, 5])):
+        b = dte.Batch(dte.BATCH_UNPACK, [(faces[j].h, 1, grid2.data_ptr(), packed.data_ptr() + offs[j]) for j in idx])
+        parts[name] = round(_mean_s(s, lambda: b.enqueue(s.cuda_stream), R, fl) * 1e6, 2)
+    a = torch.empty(24 << 20, dtype=torch.uint8, device=dev)
+    b2 = torch.empty_like(a)
+    t_copy = _mean_s(s, lambda: b2.copy_(a), R, fl)
+    _line("512^3 float64 halo faces, one at a time (axis 2 = fastest; its faces have 16-byte runs)",
+          "six-face struct pack us", round(t_pack * 1e6, 2), "us",
+          {"higher_is_better": False, "faces": res, "unpack_batch_us": parts,
+           "torch_copy_24MiB_us": round(t_copy * 1e6, 2),
+           "note": "means of 100 CUDA-event timings (8.192 us event resolution), L2 flushed before each"})
+
+
 CONFIGS = {"vector": run_config_vector, "records": run_config_records, "batch": run_config_batch,
            "largeblock": run_config_largeblock, "autograd": run_config_autograd, "serve": run_config_serve,
-           "pipeline": run_config_pipeline}
+           "pipeline": run_config_pipeline, "faces": run_config_faces}
 
 
 def main():
