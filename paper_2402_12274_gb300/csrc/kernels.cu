@@ -49,6 +49,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) move_kernel(Desc d, Op o
                                                                    Spread sp)
 {
     extern __shared__ uint4 smem[];
+    __shared__ uint4 scratch[kScratch<W>];
+    char *scr = reinterpret_cast<char *>(&scratch[W < 16 ? threadIdx.x : 0]);
     const char *blob;
     const DNode *nodes;
     stage_desc(d, smem, blob, nodes);
@@ -61,7 +63,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) move_kernel(Desc d, Op o
         const int64_t c0 = p * span;
         const int64_t c1 = min(c0 + span, nchunks);
         for (int64_t base = c0; base < c1; base += kStep)
-            warp_step<W, PACK, PK16>(op, nodes, blob, base, c1, lane, h);
+            warp_step<W, PACK, PK16>(op, nodes, blob, base, c1, lane, h, scr);
         p += sp.inc;
         if (p >= sp.nspans) p -= sp.nspans;
     }
@@ -111,6 +113,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_kernel(const Batch
 {
     extern __shared__ uint4 smem[];
     __shared__ Op wop[kWarps];  // the op each warp is working on
+    __shared__ uint4 scratch[kScratch<W>];
+    char *scr = reinterpret_cast<char *>(&scratch[W < 16 ? threadIdx.x : 0]);
     const int wid = threadIdx.x >> 5;
     if (image_bytes > 0) {
         const uint4 *s = reinterpret_cast<const uint4 *>(image);
@@ -140,7 +144,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_kernel(const Batch
             const char *blob = soff >= 0 ? reinterpret_cast<const char *>(smem) + soff : b->d.blob;
             const DNode *nodes = reinterpret_cast<const DNode *>(blob + sizeof(BlobHeader));
             int64_t base = (t - tile0[i]) * kStep;
-            warp_step<W, PACK, PK16>(wop[wid], nodes, blob, base, b->nchunks, lane, h);
+            warp_step<W, PACK, PK16>(wop[wid], nodes, blob, base, b->nchunks, lane, h, scr);
         }
     }
 }
@@ -337,6 +341,8 @@ template <bool PK16>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) adjoint_kernel(Desc d, Op op, int64_t nchunks, int64_t span)
 {
     extern __shared__ uint4 smem[];
+    __shared__ uint4 scratch[kThreads];
+    char *scr = reinterpret_cast<char *>(&scratch[threadIdx.x]);
     const char *blob;
     const DNode *nodes;
     stage_desc(d, smem, blob, nodes);
@@ -362,18 +368,19 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) adjoint_kernel(Desc d, O
                 if (c < c1) {
                     int64_t P = c * 16;
                     int nb = (int)(op.total - P < 16 ? op.total - P : 16);
-                    Chunk<4> ch;
-                    ch.v = v[u];
-                    int64_t dd = 0, rem = 0;
+                    // one descriptor walk per run (see gather_chunk)
+                    *reinterpret_cast<uint4 *>(scr) = v[u];
+                    int got = 0;
+#pragma unroll 1
+                    while (got < nb) {
+                        int64_t dd, rem;
+                        locate(op, nodes, blob, P + got, dd, rem, h);
+                        const int take = rem < (int64_t)(nb - got) ? (int)rem : nb - got;
+                        float *p = reinterpret_cast<float *>(op.user_out + dd);
 #pragma unroll
-                    for (int s = 0; s < 4; s++) {
-                        if (s * 4 < nb) {
-                            if (rem <= 0) locate(op, nodes, blob, P + s * 4, dd, rem, h);
-                            float *p = reinterpret_cast<float *>(op.user_out + dd);
-                            *p = *p + __uint_as_float(ch.w[s]);
-                            dd += 4;
-                            rem -= 4;
-                        }
+                        for (int k = 0; k < 4; k++)
+                            if (k * 4 < take) p[k] = p[k] + *reinterpret_cast<const float *>(scr + got + 4 * k);
+                        got += take;
                     }
                 }
             }

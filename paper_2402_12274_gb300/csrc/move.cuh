@@ -142,53 +142,59 @@ __device__ __forceinline__ void stw(char *p, typename Word<W>::T v)
     *reinterpret_cast<typename Word<W>::T *>(p) = v;
 }
 
-// gather the nb (<= 16) packed bytes starting at P from the user layout
+// gather the nb (<= 16) packed bytes starting at P from the user layout.
+// With W < 16 the chunk is assembled run by run in the thread's 16-byte
+// shared scratch `scr`: one descriptor walk per run, in a rolled loop, so
+// the walk is inlined once per chunk slot (inlining it once per word made
+// the kernels large enough to stall on instruction fetch).
 template <int W>
 __device__ __forceinline__ uint4 gather_chunk(const Op &op, const DNode *nodes, const char *blob, int64_t P,
-                                              int nb, Hint &h)
+                                              int nb, Hint &h, char *scr)
 {
-    Chunk<W> c;
+    using T = typename Word<W>::T;
     if (W == 16) {
         int64_t d, rem;
         locate(op, nodes, blob, P, d, rem, h);
-        c.v = ldw<16>(op.user_in + d);
-        return c.v;
+        return ldw<16>(op.user_in + d);
     }
-    c.v = make_uint4(0, 0, 0, 0);
-    int64_t d = 0, rem = 0;
+    int got = 0;
+#pragma unroll 1
+    while (got < nb) {
+        int64_t d, rem;
+        locate(op, nodes, blob, P + got, d, rem, h);
+        const int take = rem < (int64_t)(nb - got) ? (int)rem : nb - got;
+        const char *src = op.user_in + d;
 #pragma unroll
-    for (int s = 0; s < 16 / W; s++) {
-        if (s * W < nb) {
-            if (rem <= 0) locate(op, nodes, blob, P + s * W, d, rem, h);
-            c.w[s] = ldw<W>(op.user_in + d);
-            d += W;
-            rem -= W;
-        }
+        for (int k = 0; k < 16 / W; k++)
+            if (k * W < take) *reinterpret_cast<T *>(scr + got + k * W) = ldw<W>(src + k * W);
+        got += take;
     }
-    return c.v;
+    return *reinterpret_cast<const uint4 *>(scr);
 }
 
 template <int W>
 __device__ __forceinline__ void scatter_chunk(const Op &op, const DNode *nodes, const char *blob, int64_t P,
-                                              int nb, uint4 v, Hint &h)
+                                              int nb, uint4 v, Hint &h, char *scr)
 {
-    Chunk<W> c;
-    c.v = v;
+    using T = typename Word<W>::T;
     if (W == 16) {
         int64_t d, rem;
         locate(op, nodes, blob, P, d, rem, h);
-        *reinterpret_cast<uint4 *>(op.user_out + d) = c.v;
+        *reinterpret_cast<uint4 *>(op.user_out + d) = v;
         return;
     }
-    int64_t d = 0, rem = 0;
+    *reinterpret_cast<uint4 *>(scr) = v;
+    int got = 0;
+#pragma unroll 1
+    while (got < nb) {
+        int64_t d, rem;
+        locate(op, nodes, blob, P + got, d, rem, h);
+        const int take = rem < (int64_t)(nb - got) ? (int)rem : nb - got;
+        char *dst = op.user_out + d;
 #pragma unroll
-    for (int s = 0; s < 16 / W; s++) {
-        if (s * W < nb) {
-            if (rem <= 0) locate(op, nodes, blob, P + s * W, d, rem, h);
-            stw<W>(op.user_out + d, c.w[s]);
-            d += W;
-            rem -= W;
-        }
+        for (int k = 0; k < 16 / W; k++)
+            if (k * W < take) stw<W>(dst + k * W, *reinterpret_cast<const T *>(scr + got + k * W));
+        got += take;
     }
 }
 
@@ -217,6 +223,11 @@ __device__ __forceinline__ void store_packed(char *p, uint4 v, int nb)
     for (int s = 0; s < 16 / W; s++)
         if (s * W < nb) stw<W>(p + s * W, c.w[s]);
 }
+
+// The per-thread 16-byte scratch of the W < 16 chunk paths (a kernel
+// declares `__shared__ uint4 name[kScratch<W>]` and passes its slot).
+template <int W>
+constexpr int kScratch = W < 16 ? kThreads : 1;
 
 // One warp step, 16-byte words: a lane's chunks sit 512 bytes apart, so when
 // the run found for its first chunk extends past a later chunk, that chunk's
@@ -259,7 +270,7 @@ __device__ __forceinline__ void warp_step16(const Op &op, const DNode *nodes, co
 // One warp step: chunks [base, base + kStep) clipped to `end`.
 template <int W, bool PACK, bool PK16>
 __device__ __forceinline__ void warp_step(const Op &op, const DNode *nodes, const char *blob, int64_t base,
-                                          int64_t end, int lane, Hint &h)
+                                          int64_t end, int lane, Hint &h, char *scr)
 {
     if (W == 16) {
         warp_step16<PACK>(op, nodes, blob, base, end, lane, h);
@@ -272,7 +283,7 @@ __device__ __forceinline__ void warp_step(const Op &op, const DNode *nodes, cons
         if (c < end) {
             int64_t P = c * 16;
             int nb = (int)(op.total - P < 16 ? op.total - P : 16);
-            if (PACK) v[u] = gather_chunk<W>(op, nodes, blob, P, nb, h);
+            if (PACK) v[u] = gather_chunk<W>(op, nodes, blob, P, nb, h, scr);
             else v[u] = load_packed<W, PK16>(op.packed_in + P, nb);
         }
     }
@@ -283,7 +294,7 @@ __device__ __forceinline__ void warp_step(const Op &op, const DNode *nodes, cons
             int64_t P = c * 16;
             int nb = (int)(op.total - P < 16 ? op.total - P : 16);
             if (PACK) store_packed<W, PK16>(op.packed_out + P, v[u], nb);
-            else scatter_chunk<W>(op, nodes, blob, P, nb, v[u], h);
+            else scatter_chunk<W>(op, nodes, blob, P, nb, v[u], h, scr);
         }
     }
 }

@@ -70,12 +70,12 @@ __device__ __forceinline__ void st_release_sys(int64_t *p, int64_t v)
 }
 
 template <int W, bool PACK, bool PK16>
-__device__ __noinline__ void serve_chunk_tile(const BatchOp *b, int64_t t, int lane)
+__device__ __noinline__ void serve_chunk_tile(const BatchOp *b, int64_t t, int lane, char *scr)
 {
     const char *blob = b->d.blob;
     const DNode *nodes = reinterpret_cast<const DNode *>(blob + sizeof(BlobHeader));
     Hint h{-1, 0};
-    warp_step<W, PACK, PK16>(b->op, nodes, blob, t * kStep, b->nchunks, lane, h);
+    warp_step<W, PACK, PK16>(b->op, nodes, blob, t * kStep, b->nchunks, lane, h, scr);
 }
 
 template <int W, bool PACK>
@@ -88,18 +88,18 @@ __device__ __noinline__ void serve_seg_tile(const BatchOp *b, int64_t t, int lan
 }
 
 template <bool PACK>
-__device__ __forceinline__ void serve_tile_dir(const BatchOp *b, int64_t t, int lane)
+__device__ __forceinline__ void serve_tile_dir(const BatchOp *b, int64_t t, int lane, char *scr)
 {
     switch (b->wsel) {
-    case 0: serve_chunk_tile<16, PACK, true>(b, t, lane); break;
-    case 1: serve_chunk_tile<8, PACK, true>(b, t, lane); break;
-    case 2: serve_chunk_tile<8, PACK, false>(b, t, lane); break;
-    case 3: serve_chunk_tile<4, PACK, true>(b, t, lane); break;
-    case 4: serve_chunk_tile<4, PACK, false>(b, t, lane); break;
-    case 5: serve_chunk_tile<2, PACK, true>(b, t, lane); break;
-    case 6: serve_chunk_tile<2, PACK, false>(b, t, lane); break;
-    case 7: serve_chunk_tile<1, PACK, true>(b, t, lane); break;
-    case 8: serve_chunk_tile<1, PACK, false>(b, t, lane); break;
+    case 0: serve_chunk_tile<16, PACK, true>(b, t, lane, scr); break;
+    case 1: serve_chunk_tile<8, PACK, true>(b, t, lane, scr); break;
+    case 2: serve_chunk_tile<8, PACK, false>(b, t, lane, scr); break;
+    case 3: serve_chunk_tile<4, PACK, true>(b, t, lane, scr); break;
+    case 4: serve_chunk_tile<4, PACK, false>(b, t, lane, scr); break;
+    case 5: serve_chunk_tile<2, PACK, true>(b, t, lane, scr); break;
+    case 6: serve_chunk_tile<2, PACK, false>(b, t, lane, scr); break;
+    case 7: serve_chunk_tile<1, PACK, true>(b, t, lane, scr); break;
+    case 8: serve_chunk_tile<1, PACK, false>(b, t, lane, scr); break;
     case 9: serve_seg_tile<8, PACK>(b, t, lane); break;
     case 10: serve_seg_tile<4, PACK>(b, t, lane); break;
     case 11: serve_seg_tile<2, PACK>(b, t, lane); break;
@@ -143,6 +143,8 @@ __global__ void __launch_bounds__(kThreads, 2)
                  unsigned long long *done, SlotRec *dring, int64_t *comp, int64_t span, int64_t idle_budget_ns)
 {
     __shared__ BatchOp wop[kWarps];
+    __shared__ uint4 scratch[kThreads];  // chunk assembly for the sub-16-byte word classes
+    char *scr = reinterpret_cast<char *>(&scratch[threadIdx.x]);
     __shared__ int32_t wkind[kWarps];
     __shared__ int64_t wntiles[kWarps];
     const unsigned FULL = 0xffffffffu;
@@ -235,8 +237,8 @@ __global__ void __launch_bounds__(kThreads, 2)
         cached = r;
         const bool pack = wkind[w] == DTE_BATCH_PACK;
         for (int64_t tt = t; tt < t + k; tt++) {
-            if (pack) serve_tile_dir<true>(&wop[w], tt, lane);
-            else serve_tile_dir<false>(&wop[w], tt, lane);
+            if (pack) serve_tile_dir<true>(&wop[w], tt, lane, scr);
+            else serve_tile_dir<false>(&wop[w], tt, lane, scr);
         }
         __threadfence();
         __syncwarp();
