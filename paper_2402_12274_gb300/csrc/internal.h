@@ -100,6 +100,7 @@ struct Committed {
     int64_t bytes = 0;
     int64_t align = 16;            // type alignment class (<= 16)
     int64_t maxrun = 0;            // longest raw run of the descriptor
+    bool big_list = false;         // a LIST level of more than 32 entries (searched, not divided)
     int64_t nseg = 0, size = 0;
     bool nonoverlap = true;        // structural proof for one element
     int overlap_exact = -1;        // -1 unknown, 0 no, 1 yes (one element)

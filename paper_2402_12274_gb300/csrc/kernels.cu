@@ -454,7 +454,7 @@ static int launch_move(bool pack, dte_type t, const char *dblob, const void *use
     if (occ == 0) occ = occupancy(k, d.stage == STAGE_BLOB ? (size_t)kSmemBlob : smem);
     int64_t max_blocks = (int64_t)sm_count(dev) * occ;
     int64_t max_warps = max_blocks * kWarps;
-    if (W < 16 && c.maxrun <= kSegMaxRun) {
+    if (use_seg_major(c, W)) {
         // short runs, small words: one decode per segment, cooperative copy
         typedef void (*SegKernel)(Desc, Op, int64_t, FastDiv, int64_t, int64_t, int64_t);
         SegKernel sk;

@@ -28,7 +28,16 @@ constexpr int kStep = 32 * kU;        // chunks per warp step (2 KiB)
 #endif
 constexpr int kMinBlocks = DTE_MINBLOCKS;  // CTAs per SM the data kernels are sized for (<= 64 regs)
 constexpr int64_t kSmemBlob = 16384;  // stage descriptors up to this size whole
-constexpr int64_t kSegMaxRun = 256;   // segment-major kernel for runs up to this length
+// Segment-major movement pays off for short runs under a large index table
+// (one direct table lookup per segment instead of a search per run); for
+// strided layouts (divisions only) the chunk-major kernel is faster even
+// with short runs.
+constexpr int64_t kSegMaxRun = 256;
+
+static bool use_seg_major(const Committed &c, int W)
+{
+    return W < 16 && c.maxrun <= kSegMaxRun && c.big_list;
+}
 constexpr int kMaxSmemNodes = 64;
 
 enum : int { STAGE_NONE = 0, STAGE_NODES = 1, STAGE_BLOB = 2 };
@@ -519,7 +528,7 @@ static void fill_batch_op(BatchOp &h, const Committed &c, int64_t extent, const 
     h.op = make_op(c, extent, o.user, o.packed, o.count);
     h.nchunks = (h.op.total + 15) / 16;
     int W = word_of(c, extent, o.count, o.user, o.packed);
-    if (W < 16 && c.maxrun <= kSegMaxRun) {
+    if (use_seg_major(c, W)) {
         h.wsel = seg_class(W);
         h.nseg_elem = c.nseg;
         h.nsegs = o.count * c.nseg;

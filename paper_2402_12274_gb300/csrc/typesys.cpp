@@ -459,6 +459,7 @@ std::shared_ptr<Committed> commit_node(const NP &root)
     DNode *dn = reinterpret_cast<DNode *>(blob + sizeof(BlobHeader));
     for (size_t i = 0; i < order.size(); i++) {
         const Node *n = order[i];
+        if (n->kind == NK_LIST && n->count > 32) C->big_list = true;
         DNode d;
         std::memset(&d, 0, sizeof d);
         d.kind = n->kind;

@@ -77,6 +77,20 @@ def test_merging_layouts_pack_unpack():
         check_move(inputs.sequential_spec(rng), int(rng.integers(1, 4)), rng)
 
 
+@pytest.mark.parametrize("el", ["byte", "int16", "float32", "float64"])
+def test_short_runs_under_index_tables(el):
+    # indexed lists longer than 32 entries with short blocks take the
+    # segment-major kernel (one word class per element size)
+    rng = np.random.default_rng(205)
+    for n in (33, 200, 3000):
+        bl = rng.integers(1, 6, n)
+        disp = np.cumsum(bl + rng.integers(0, 4, n)) - bl
+        spec = ("indexed", bl.astype(np.int64), disp.astype(np.int64), ("basic", el))
+        for count in (1, 3):
+            check_move(spec, count, rng, misalign=False)
+            check_move(spec, count, rng)
+
+
 def test_darray_pack_unpack():
     rng = np.random.default_rng(204)
     for _ in range(200):

@@ -75,6 +75,17 @@ def test_range_moves_each_word_size(el, bl, st):
         check_ranges(("vector", 3000, bl, st, ("basic", el)), count, rng)
 
 
+@pytest.mark.parametrize("el", ["byte", "bfloat16", "float32", "float64"])
+def test_range_moves_short_runs_under_index_tables(el):
+    # segment-major kernel: windows clip its first and last segment
+    rng = np.random.default_rng(307)
+    bl = rng.integers(1, 6, 2000)
+    disp = np.cumsum(bl + rng.integers(0, 4, 2000)) - bl
+    spec = ("indexed", bl.astype(np.int64), disp.astype(np.int64), ("basic", el))
+    for count in (1, 2):
+        check_ranges(spec, count, rng)
+
+
 def sendrecv_case(sspec, rspec, scount, staging_bytes, rng):
     ts, os_ = both(sspec)
     tr, or_ = both(rspec)
