@@ -339,15 +339,18 @@ __device__ __forceinline__ void seg_round(const Op &op, const DNode *nodes, cons
         int64_t ud[kU];
 #pragma unroll
         for (int u = 0; u < kU; u++) {
+            // segment of each word of this 32-word window: the segments that
+            // start before the window, plus those starting in it up to the
+            // word (a bit mask of start positions, one OR-reduction)
+            const int64_t qa = p0 + (w0 + u * 32) * W;
             const int64_t wi = w0 + u * 32 + lane;
-            const int64_t q = p0 + wi * W;
-            int lo = 0;
-#pragma unroll
-            for (int step = 16; step >= 1; step >>= 1) {
-                const int cand = lo + step;
-                const int64_t pc = __shfl_sync(FULL, ps, cand & 31);
-                if (cand < nvalid && pc <= q) lo = cand;
-            }
+            const int64_t q = qa + (int64_t)lane * W;
+            const bool valid = lane < nvalid;
+            const int before = __popc(__ballot_sync(FULL, valid && ps < qa)) - 1;
+            const int64_t rel = ps - qa;
+            const unsigned bit = (valid && rel >= 0 && rel < 32 * W) ? 1u << (int)(rel / W) : 0u;
+            const unsigned starts = __reduce_or_sync(FULL, bit);
+            const int lo = before + __popc(starts & (0xffffffffu >> (31 - lane)));
             ud[u] = __shfl_sync(FULL, disp, lo) + (q - __shfl_sync(FULL, ps, lo));
             if (wi < nwords) {
                 if (PACK) v[u] = ldw<W>(op.user_in + ud[u]);
