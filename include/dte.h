@@ -380,6 +380,13 @@ DTE_API int dte_unpack_batch_enqueue(int64_t nops, const dte_op *ops, dte_stream
  * Returns as soon as the work is queued on `stream`. */
 DTE_API int dte_pack_batch_enqueue_noalloc(int64_t nops, const dte_op *ops, dte_stream_t stream);
 
+/* Number of bounded device waits that gave up on the current device since
+ * the library was loaded (the bulk-copy kernels wait on shared-memory
+ * barriers with a time budget of about a second; a wait that runs out is
+ * counted here and the kernel drains what it issued and returns instead of
+ * hanging).  Synchronises with the device.  Expected to stay 0. */
+DTE_API int dte_device_timeouts(int64_t *count);
+
 /* ------------------------------------------------------------------------
  * Request loop: a device-resident stand-in for the progress engine (§7
  * general progress, §2 polled generalized requests, §5 work executed in the

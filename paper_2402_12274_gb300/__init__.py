@@ -107,6 +107,7 @@ _SIGS = {
     "dte_pack_range_enqueue": ([_p, _i64, _p, _i64, _i64, _p, _p], C.c_int),
     "dte_unpack_range_enqueue": ([_p, _i64, _i64, _p, _i64, _p, _p], C.c_int),
     "dte_sendrecv_enqueue": ([_p, _i64, _p, _p, _i64, _p, _p, _i64, _p], C.c_int),
+    "dte_device_timeouts": ([_pi64], C.c_int),
     "dte_batch_create": ([C.c_int, _i64, C.POINTER(dte_op), _pp], C.c_int),
     "dte_batch_set_launch": ([_p, C.c_int, _i64], C.c_int),
     "dte_batch_enqueue": ([_p, _p], C.c_int),
@@ -364,6 +365,12 @@ def dte_sendrecv_enqueue(sendbuf: int, sendcount: int, sendtype: int, recvbuf: i
                          recvtype: int, staging: int, staging_bytes: int, stream: int = 0) -> None:
     _ck(lib.dte_sendrecv_enqueue(sendbuf, sendcount, sendtype, recvbuf, recvcount, recvtype, staging,
                                  staging_bytes, stream), "dte_sendrecv_enqueue")
+
+
+def dte_device_timeouts() -> int:
+    n = C.c_int64()
+    _ck(lib.dte_device_timeouts(C.byref(n)), "dte_device_timeouts")
+    return n.value
 
 
 def _ops_array(ops):

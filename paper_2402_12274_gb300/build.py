@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libdte.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
 
 SOURCES = ["typesys.cpp", "kernels.cu", "server.cu"]
-HEADERS = ["desc.h", "internal.h", "move.cuh"]
+HEADERS = ["desc.h", "internal.h", "move.cuh", "bulk.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2,-fvisibility=hidden",
           "-I", os.path.join(ROOT, "include")]

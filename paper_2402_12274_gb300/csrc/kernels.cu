@@ -30,11 +30,13 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstddef>
 #include <cstring>
 #include <numeric>
 #include <vector>
 
+#include "bulk.cuh"
 #include "internal.h"
 #include "move.cuh"
 
@@ -422,6 +424,19 @@ static MoveKernel pick_move(int W, bool pk16)
     }
 }
 
+// The bulk kernels use more than the default 48 KiB of dynamic shared
+// memory (stages + staged descriptor); raised once per device.
+static void allow_bulk_smem(int dev)
+{
+    static std::atomic<bool> done[64];
+    if (done[dev & 63].load(std::memory_order_acquire)) return;
+    const int bytes = (int)(kSmemBlob + 128 + kBulkSmem);
+    cudaFuncSetAttribute(bulk_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(bulk_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaGetLastError();
+    done[dev & 63].store(true, std::memory_order_release);
+}
+
 // Count-level index of the segment holding packed-stream byte B (< count*size).
 static int64_t segment_of(const Committed &c, int64_t B)
 {
@@ -476,6 +491,19 @@ static int launch_move(bool pack, dte_type t, const char *dblob, const void *use
                                                                 (int64_t)sm_count(dev) * socc));
         sk<<<(unsigned)blocks, kThreads, smem, stream>>>(d, op, c.nseg, c.nodes()[c.root].div_nseg, seg0, nsegs,
                                                         32 * span_rounds);
+        if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
+        return DTE_SUCCESS;
+    }
+    if (kBulk && W == 16 && nbytes >= kBulkMinBytes && c.nseg > 0 && c.size / c.nseg >= kBulkMinRun) {
+        // long runs: bulk copies by the copy engine of each SM (bulk.cuh)
+        allow_bulk_smem(dev);
+        const int64_t buf_off = ((int64_t)smem + 127) & ~(int64_t)127;
+        const int64_t ntiles = (nbytes + kBulkTile - 1) / kBulkTile;
+        const int64_t blocks =
+            std::max<int64_t>(1, std::min<int64_t>((ntiles + kBulkWarps - 1) / kBulkWarps, sm_count(dev)));
+        auto bk = pack ? bulk_kernel<true> : bulk_kernel<false>;
+        bk<<<(unsigned)blocks, kBulkWarps * 32, (size_t)(buf_off + kBulkSmem), stream>>>(d, op, ntiles,
+                                                                                         (int32_t)buf_off);
         if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
         return DTE_SUCCESS;
     }
@@ -1338,4 +1366,17 @@ extern "C" int dte_pack_adjoint_f32_enqueue(const void *gy, int64_t count, dte_t
     } catch (...) {
         return DTE_ERR_NOMEM;
     }
+}
+
+// Bounded device waits that gave up (bulk kernels), on the current device.
+extern "C" int dte_device_timeouts(int64_t *count)
+{
+    if (!count) return DTE_ERR_ARG;
+    unsigned long long v = 0;
+    if (cudaMemcpyFromSymbol(&v, dte::g_bulk_timeouts, sizeof v) != cudaSuccess) {
+        cudaGetLastError();
+        return DTE_ERR_CUDA;
+    }
+    *count = (int64_t)v;
+    return DTE_SUCCESS;
 }

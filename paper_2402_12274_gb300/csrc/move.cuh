@@ -281,29 +281,29 @@ template <int W, bool PACK, bool PK16>
 __device__ __forceinline__ void warp_step(const Op &op, const DNode *nodes, const char *blob, int64_t base,
                                           int64_t end, int lane, Hint &h, char *scr)
 {
-    if (W == 16) {
+    if constexpr (W == 16) {
         warp_step16<PACK>(op, nodes, blob, base, end, lane, h);
-        return;
-    }
-    uint4 v[kU];
+    } else {
+        uint4 v[kU];
 #pragma unroll
-    for (int u = 0; u < kU; u++) {
-        int64_t c = base + u * 32 + lane;
-        if (c < end) {
-            int64_t P = c * 16;
-            int nb = (int)(op.total - P < 16 ? op.total - P : 16);
-            if (PACK) v[u] = gather_chunk<W>(op, nodes, blob, P, nb, h, scr);
-            else v[u] = load_packed<W, PK16>(op.packed_in + P, nb);
+        for (int u = 0; u < kU; u++) {
+            int64_t c = base + u * 32 + lane;
+            if (c < end) {
+                int64_t P = c * 16;
+                int nb = (int)(op.total - P < 16 ? op.total - P : 16);
+                if (PACK) v[u] = gather_chunk<W>(op, nodes, blob, P, nb, h, scr);
+                else v[u] = load_packed<W, PK16>(op.packed_in + P, nb);
+            }
         }
-    }
 #pragma unroll
-    for (int u = 0; u < kU; u++) {
-        int64_t c = base + u * 32 + lane;
-        if (c < end) {
-            int64_t P = c * 16;
-            int nb = (int)(op.total - P < 16 ? op.total - P : 16);
-            if (PACK) store_packed<W, PK16>(op.packed_out + P, v[u], nb);
-            else scatter_chunk<W>(op, nodes, blob, P, nb, v[u], h, scr);
+        for (int u = 0; u < kU; u++) {
+            int64_t c = base + u * 32 + lane;
+            if (c < end) {
+                int64_t P = c * 16;
+                int nb = (int)(op.total - P < 16 ? op.total - P : 16);
+                if (PACK) store_packed<W, PK16>(op.packed_out + P, v[u], nb);
+                else scatter_chunk<W>(op, nodes, blob, P, nb, v[u], h, scr);
+            }
         }
     }
 }

@@ -77,6 +77,22 @@ def test_merging_layouts_pack_unpack():
         check_move(inputs.sequential_spec(rng), int(rng.integers(1, 4)), rng)
 
 
+@pytest.mark.parametrize("L", [2048, 4096 + 16, 65536, 1 << 20])
+def test_long_runs_take_bulk_copies(L):
+    # runs of L bytes (16-byte multiples, 16-byte aligned buffers) in moves of
+    # at least 1 MiB go through the bulk-copy kernels; no bounded wait gives up
+    rng = np.random.default_rng(210)
+    n = max(2, (3 << 20) // L)
+    spec = ("hvector", n, 1, L + 768, ("contig", L // 8, ("basic", "float64")))
+    for count in (1, 2):
+        check_move(spec, count, rng, misalign=False)
+    # a struct of long and short runs still averages long runs per segment
+    spec = ("struct", [1, 1], [0, 8 << 20], [("contig", (6 << 20) // 8, ("basic", "float64")),
+                                              ("vector", 64, 2, 4, ("basic", "float64"))])
+    check_move(spec, 1, rng, misalign=False)
+    assert dte.dte_device_timeouts() == 0
+
+
 @pytest.mark.parametrize("el", ["byte", "int16", "float32", "float64"])
 def test_short_runs_under_index_tables(el):
     # indexed lists longer than 32 entries with short blocks take the
@@ -462,3 +478,39 @@ def test_per_call_enqueue_under_graph_capture():
     g.replay()
     torch.cuda.synchronize()
     assert np.array_equal(d_pk.cpu().numpy(), o.pack(src, 1))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("launch", [(0, 1), (0, 8), (3, 4)])
+def test_full_size_batch_sampled_against_oracle(launch):
+    # the 10^4-op pack batch of the batch benchmark (same generator and seed,
+    # 3.9 GB packed), in several launch shapes; a sample of ops is checked
+    # byte for byte against the oracle, and every op against its own span
+    rng = np.random.default_rng(4)
+    specs = inputs.batch_specs(rng, 10_000)
+    types = [dte.Datatype.from_spec(sp).commit() for sp, _ in specs]
+    spans = [t.true_lb + t.true_extent for t in types]
+    sizes = [t.size for t in types]
+    up = lambda v: (v + 255) // 256 * 256  # noqa: E731
+    so = np.concatenate([[0], np.cumsum([up(v) for v in spans])])
+    po = np.concatenate([[0], np.cumsum([up(v) for v in sizes])])
+    src = torch.empty(int(so[-1]), dtype=torch.uint8, device=DEV)
+    src.random_(0, 256)
+    pk = torch.full((int(po[-1]),), SENT, dtype=torch.uint8, device=DEV)
+    b = dte.Batch(dte.BATCH_PACK, [(t.h, 1, src.data_ptr() + int(a), pk.data_ptr() + int(c))
+                                   for t, a, c in zip(types, so, po)])
+    b.set_launch(*launch)
+    b.enqueue(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    pick = np.random.default_rng(5).choice(len(types), 40, replace=False)
+    for i in pick:
+        o = oracle.from_spec(specs[i][0])
+        s_i = src[int(so[i]):int(so[i]) + spans[i]].cpu().numpy()
+        got = pk[int(po[i]):int(po[i]) + sizes[i]].cpu().numpy()
+        assert np.array_equal(got, o.pack(s_i, 1)), (i, specs[i][0][0])
+    # nothing written between ops: the sentinel survives in every gap
+    gaps = torch.ones(int(po[-1]), dtype=torch.bool, device=DEV)
+    for c, z in zip(po[:-1], sizes):
+        gaps[int(c):int(c) + z] = False
+    assert bool((pk[gaps] == SENT).all())
+    b.free()

@@ -86,6 +86,32 @@ def test_range_moves_short_runs_under_index_tables(el):
         check_ranges(spec, count, rng)
 
 
+def test_range_moves_long_runs_bulk_copies():
+    # 16-byte aligned windows of at least 1 MiB over long runs take the
+    # bulk-copy kernels; odd windows fall back to the chunk kernels
+    rng = np.random.default_rng(308)
+    spec = ("hvector", 40, 1, 96 << 10, ("contig", 8192, ("basic", "float64")))
+    t, o = both(spec)
+    total = o.size
+    lo, hi = span_of(o, 1)
+    src = rng.integers(0, 256, hi, dtype=np.uint8)
+    d_src = torch.from_numpy(src).to(DEV)
+    full = o.pack(src, 1)
+    s = torch.cuda.current_stream()
+    for a, n in ((0, total), (16 * 4097, 1 << 20), (16 * 12345, total - 16 * 12345 - 16 * 77),
+                 (4096, (1 << 20) + 16), (8, 1 << 20)):
+        out = torch.full((n + 16,), SENT, dtype=torch.uint8, device=DEV)
+        dte.pack_range(d_src, 1, t, a, n, out, s)
+        got = out.cpu().numpy()
+        assert np.array_equal(got[:n], full[a:a + n]) and np.all(got[n:] == SENT)
+        want = np.full(hi, SENT, np.uint8)
+        o.unpack_range(full[a:a + n], a, 1, want)
+        d_dst = torch.full((hi,), SENT, dtype=torch.uint8, device=DEV)
+        dte.unpack_range(torch.from_numpy(full[a:a + n].copy()).to(DEV), a, n, d_dst, 1, t, s)
+        assert np.array_equal(d_dst.cpu().numpy(), want)
+    assert dte.dte_device_timeouts() == 0
+
+
 def sendrecv_case(sspec, rspec, scount, staging_bytes, rng):
     ts, os_ = both(sspec)
     tr, or_ = both(rspec)
