@@ -6,21 +6,24 @@
 // §5.3), §5.2 (send/recv of (buf, count, datatype)), §3.1 (iov queries).
 //
 // Data movement design (pure data movement, no tensor cores):
-//  * The packed side is contiguous, so work is split in packed space: each
-//    warp owns a contiguous range of 2 KiB steps; lane l of the warp handles
-//    chunks l, l+32, l+64, l+96 (16 bytes each) of a step, so every
-//    packed-side access of a warp is one coalesced 512-byte transaction, and
-//    four independent 16-byte loads per lane are in flight before the stores.
+//  * The packed side is contiguous, so work is split in packed space into
+//    2 KiB warp steps; lane l of the warp handles chunks l, l+32, l+64, l+96
+//    (16 bytes each) of a step, so every packed-side access of a warp is one
+//    coalesced 512-byte transaction, and four independent 16-byte loads per
+//    lane are in flight before the stores.  Warps take spans of steps in a
+//    spread order (Spread, move.cuh).
 //  * Each chunk maps back to the user layout through the committed descriptor
 //    (desc.h: REG levels by fast invariant division, LIST levels by a search
-//    that gallops from that chunk slot's previous position).  Descriptors of
-//    up to 16 KiB are staged whole in shared memory; larger ones stage their
-//    node table and read index arrays through L1/L2.
+//    that gallops from the step's previous position).  Descriptors of up to
+//    16 KiB are staged whole in shared memory; larger ones stage their node
+//    table and read index arrays through L1/L2.
 //  * W, the copy word, is the largest power of two <= 16 dividing every run
 //    length and displacement of the type and both buffer addresses; a word
 //    never straddles two runs, so W = 16 moves each chunk with one 16-byte
-//    load and one 16-byte store.  Smaller W assembles the chunk from W-byte
-//    words, re-walking the descriptor only when a run ends.
+//    load and one 16-byte store.  Smaller W assembles the chunk run by run
+//    from W-byte words.
+//  * Short runs under large index tables move segment-major (seg_kernel);
+//    long runs with W = 16 move by TMA bulk copies (bulk_kernel, bulk.cuh).
 //  * Bytes are moved verbatim through integer registers: no value is ever
 //    converted, so NaN payloads survive.
 //  * Batches: many independent operations (different types, buffers and
@@ -71,13 +74,13 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) move_kernel(Desc d, Op o
     }
 }
 
-// Segment-major movement for layouts of short runs moved in words of fewer
-// than 16 bytes.  Each lane walks the descriptor once per round for one whole
-// segment (a single convergent decode per lane instead of one per run end
-// inside a chunk), then the warp moves the packed range its 32 segments cover
+// Segment-major movement for short runs (words of fewer than 16 bytes) under
+// a large index table.  Each lane walks the descriptor once per round for one
+// whole segment (a direct table lookup instead of a search per run end inside
+// a chunk), then the warp moves the packed range its 32 segments cover
 // together: lane l takes words l, l+32, l+64, l+96 of each 128-word slice and
-// finds the segment of each word with a 5-step shuffle search over the
-// lanes' packed start offsets, so packed-side accesses stay coalesced.
+// finds the segment of each word from a bit mask of the segment starts in its
+// 32-word window (seg_round), so packed-side accesses stay coalesced.
 // Segments [seg0, seg0 + nsegs) of the count-level segment list are moved;
 // a range move clips the first and last of them to its packed window.
 template <int W, bool PACK>
