@@ -45,7 +45,7 @@
 
 namespace dte {
 
-// Warps take spans of `span` chunks (a multiple of kStep) in the spread
+// Warps take spans of `span` chunks (a multiple of the step) in the spread
 // order (see Spread), so costly and cheap regions of a layout are worked on
 // at the same time, while a span keeps consecutive steps together for the
 // search hints.
@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) move_kernel(Desc d, Op o
     for (int64_t j = warp; j < sp.nspans; j += nwarps) {
         const int64_t c0 = p * span;
         const int64_t c1 = min(c0 + span, nchunks);
-        for (int64_t base = c0; base < c1; base += kStep)
+        for (int64_t base = c0; base < c1; base += kStepOf<W>)
             warp_step<W, PACK, PK16>(op, nodes, blob, base, c1, lane, h, scr);
         p += sp.inc;
         if (p >= sp.nspans) p -= sp.nspans;
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_kernel(const Batch
             const int soff = b->soff;
             const char *blob = soff >= 0 ? reinterpret_cast<const char *>(smem) + soff : b->d.blob;
             const DNode *nodes = reinterpret_cast<const DNode *>(blob + sizeof(BlobHeader));
-            int64_t base = (t - tile0[i]) * kStep;
+            int64_t base = (t - tile0[i]) * kStepOf<W>;
             warp_step<W, PACK, PK16>(wop[wid], nodes, blob, base, b->nchunks, lane, h, scr);
         }
     }
@@ -511,7 +511,8 @@ static int launch_move(bool pack, dte_type t, const char *dblob, const void *use
         return DTE_SUCCESS;
     }
     int64_t nchunks = (op.total + 15) / 16;
-    int64_t steps = (nchunks + kStep - 1) / kStep;
+    const int64_t step = step_of_word(W);
+    int64_t steps = (nchunks + step - 1) / step;
     // span: one step when the descriptor sits in shared memory; up to eight
     // when index tables are searched in global memory (consecutive steps
     // reuse the search position), but never so many that warps go idle
@@ -519,7 +520,7 @@ static int launch_move(bool pack, dte_type t, const char *dblob, const void *use
     int64_t units = (steps + span_steps - 1) / span_steps;
     int64_t blocks = std::min<int64_t>((units + kWarps - 1) / kWarps, max_blocks);
     if (blocks < 1) blocks = 1;
-    k<<<(unsigned)blocks, kThreads, smem, stream>>>(d, op, nchunks, span_steps * kStep,
+    k<<<(unsigned)blocks, kThreads, smem, stream>>>(d, op, nchunks, span_steps * step,
                                                     make_spread(units, blocks * kWarps));
     if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
     return DTE_SUCCESS;

@@ -23,6 +23,18 @@ constexpr int kWarps = kThreads / 32;
 #endif
 constexpr int kU = DTE_KU;            // chunks per lane per step
 constexpr int kStep = 32 * kU;        // chunks per warp step (2 KiB)
+// 16-byte moves take half-size steps (1 KiB: two chunks per lane): each
+// chunk is one load and one store, so finer steps balance the warps better
+// at the end of a launch; the sub-16-byte paths keep four chunks per lane to
+// overlap their per-run descriptor walks.
+#ifndef DTE_KU16
+#define DTE_KU16 2
+#endif
+template <int W>
+constexpr int kUOf = W == 16 ? DTE_KU16 : kU;
+template <int W>
+constexpr int kStepOf = 32 * kUOf<W>;
+static inline int64_t step_of_word(int W) { return W == 16 ? kStepOf<16> : kStep; }
 #ifndef DTE_MINBLOCKS
 #define DTE_MINBLOCKS 4
 #endif
@@ -245,11 +257,11 @@ template <bool PACK>
 __device__ __forceinline__ void warp_step16(const Op &op, const DNode *nodes, const char *blob, int64_t base,
                                             int64_t end, int lane, Hint &h)
 {
-    uint4 v[kU];
-    int64_t d[kU];
+    uint4 v[kUOf<16>];
+    int64_t d[kUOf<16>];
     int64_t d0 = 0, rem0 = 0;
 #pragma unroll
-    for (int u = 0; u < kU; u++) {
+    for (int u = 0; u < kUOf<16>; u++) {
         int64_t c = base + u * 32 + lane;
         if (c < end) {
             if (u > 0 && rem0 >= (int64_t)u * 512 + 16) {
@@ -267,7 +279,7 @@ __device__ __forceinline__ void warp_step16(const Op &op, const DNode *nodes, co
         }
     }
 #pragma unroll
-    for (int u = 0; u < kU; u++) {
+    for (int u = 0; u < kUOf<16>; u++) {
         int64_t c = base + u * 32 + lane;
         if (c < end) {
             if (PACK) *reinterpret_cast<uint4 *>(op.packed_out + c * 16) = v[u];
@@ -276,7 +288,7 @@ __device__ __forceinline__ void warp_step16(const Op &op, const DNode *nodes, co
     }
 }
 
-// One warp step: chunks [base, base + kStep) clipped to `end`.
+// One warp step: chunks [base, base + kStepOf<W>) clipped to `end`.
 template <int W, bool PACK, bool PK16>
 __device__ __forceinline__ void warp_step(const Op &op, const DNode *nodes, const char *blob, int64_t base,
                                           int64_t end, int lane, Hint &h, char *scr)
@@ -545,7 +557,8 @@ static void fill_batch_op(BatchOp &h, const Committed &c, int64_t extent, const 
 static int64_t op_tiles(const BatchOp &h)
 {
     if (h.wsel >= 9) return (h.nsegs + 31) / 32;
-    return (h.nchunks + kStep - 1) / kStep;
+    const int64_t st = h.wsel == 0 ? kStepOf<16> : kStep;  // class 0 is the 16-byte word
+    return (h.nchunks + st - 1) / st;
 }
 
 }  // namespace dte

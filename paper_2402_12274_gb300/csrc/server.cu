@@ -75,7 +75,7 @@ __device__ __noinline__ void serve_chunk_tile(const BatchOp *b, int64_t t, int l
     const char *blob = b->d.blob;
     const DNode *nodes = reinterpret_cast<const DNode *>(blob + sizeof(BlobHeader));
     Hint h{-1, 0};
-    warp_step<W, PACK, PK16>(b->op, nodes, blob, t * kStep, b->nchunks, lane, h, scr);
+    warp_step<W, PACK, PK16>(b->op, nodes, blob, t * kStepOf<W>, b->nchunks, lane, h, scr);
 }
 
 template <int W, bool PACK>
