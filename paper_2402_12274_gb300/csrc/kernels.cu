@@ -440,6 +440,19 @@ static void allow_bulk_smem(int dev)
     done[dev & 63].store(true, std::memory_order_release);
 }
 
+// The bulk copies are used only between buffers in device memory; pinned or
+// managed host memory (which the other kernels read and write directly)
+// keeps the chunk-major path.
+static bool device_memory(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice;
+}
+
 // Count-level index of the segment holding packed-stream byte B (< count*size).
 static int64_t segment_of(const Committed &c, int64_t B)
 {
@@ -497,7 +510,8 @@ static int launch_move(bool pack, dte_type t, const char *dblob, const void *use
         if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
         return DTE_SUCCESS;
     }
-    if (kBulk && W == 16 && nbytes >= kBulkMinBytes && c.nseg > 0 && c.size / c.nseg >= kBulkMinRun) {
+    if (kBulk && W == 16 && nbytes >= kBulkMinBytes && c.nseg > 0 && c.size / c.nseg >= kBulkMinRun &&
+        device_memory(user) && device_memory(packed)) {
         // long runs: bulk copies by the copy engine of each SM (bulk.cuh)
         allow_bulk_smem(dev);
         const int64_t buf_off = ((int64_t)smem + 127) & ~(int64_t)127;

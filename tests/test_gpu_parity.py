@@ -93,6 +93,28 @@ def test_long_runs_take_bulk_copies(L):
     assert dte.dte_device_timeouts() == 0
 
 
+def test_long_runs_from_pinned_host_memory():
+    # host buffers take the chunk kernels (bulk copies only run between
+    # device buffers); results as from device memory
+    rng = np.random.default_rng(211)
+    spec = ("hvector", 48, 1, 64 << 10, ("contig", 4096, ("basic", "float64")))
+    t, o = both(spec)
+    lo, hi = span_of(o, 1)
+    src = rng.integers(0, 256, hi, dtype=np.uint8)
+    h_src = torch.from_numpy(src).pin_memory()
+    h_pk = torch.full((o.size,), SENT, dtype=torch.uint8).pin_memory()
+    s = torch.cuda.current_stream()
+    dte.pack(h_src, 1, t, h_pk, 0, s)
+    s.synchronize()
+    assert np.array_equal(h_pk.numpy(), o.pack(src, 1))
+    h_dst = torch.full((hi,), SENT, dtype=torch.uint8).pin_memory()
+    dte.unpack(h_pk, 0, h_dst, 1, t, s)
+    s.synchronize()
+    want = np.full(hi, SENT, np.uint8)
+    o.unpack(o.pack(src, 1), 1, want)
+    assert np.array_equal(h_dst.numpy(), want)
+
+
 @pytest.mark.parametrize("el", ["byte", "int16", "float32", "float64"])
 def test_short_runs_under_index_tables(el):
     # indexed lists longer than 32 entries with short blocks take the
