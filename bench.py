@@ -732,6 +732,7 @@ def run_config_serve(args):
         dte.dte_server_wait(srv, submit(i), 60_000_000)
     t0 = time.perf_counter()
     tks = [submit(i) for i in range(nreq)]
+    t_sub = time.perf_counter() - t0
     for tk in tks:
         dte.dte_server_wait(srv, tk, 600_000_000)
     t_all = time.perf_counter() - t0
@@ -766,6 +767,7 @@ def run_config_serve(args):
     _line(f"request loop, {nreq} Poisson-arriving pack/unpack requests of 1 KiB-64 MiB, 8 GiB cap",
           "p99 latency at rho=0.8 (ms)", res["0.8"]["p99_ms"], "ms",
           {"higher_is_better": False, "service_rate_req_per_s": round(mu, 1),
+           "host_submit_us_per_request": round(t_sub / nreq * 1e6, 2),
            "service_GBs": round(float(nbytes.sum()) / t_all / 1e9, 1), "by_load": res,
            "mean_request_bytes_moved": round(float(nbytes.mean()))})
 

@@ -69,41 +69,45 @@ __device__ __forceinline__ void st_release_sys(int64_t *p, int64_t v)
     asm volatile("st.release.sys.global.s64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// One claimed span of tiles [t, t + k) of a request, out of line (one copy of
+// each variant for the whole loop, one call per claim).  The search hint h
+// is the warp's, kept while it works on the same request, so consecutive
+// tiles of a large index table continue the search where it stopped.
 template <int W, bool PACK, bool PK16>
-__device__ __noinline__ void serve_chunk_tile(const BatchOp *b, int64_t t, int lane, char *scr)
+__device__ __noinline__ void serve_chunk_span(const BatchOp *b, int64_t t, int64_t k, int lane, char *scr, Hint &h)
 {
     const char *blob = b->d.blob;
     const DNode *nodes = reinterpret_cast<const DNode *>(blob + sizeof(BlobHeader));
-    Hint h{-1, 0};
-    warp_step<W, PACK, PK16>(b->op, nodes, blob, t * kStepOf<W>, b->nchunks, lane, h, scr);
+    for (int64_t tt = t; tt < t + k; tt++)
+        warp_step<W, PACK, PK16>(b->op, nodes, blob, tt * kStepOf<W>, b->nchunks, lane, h, scr);
 }
 
 template <int W, bool PACK>
-__device__ __noinline__ void serve_seg_tile(const BatchOp *b, int64_t t, int lane)
+__device__ __noinline__ void serve_seg_span(const BatchOp *b, int64_t t, int64_t k, int lane, Hint &h)
 {
     const char *blob = b->d.blob;
     const DNode *nodes = reinterpret_cast<const DNode *>(blob + sizeof(BlobHeader));
-    Hint h{-1, 0};
-    seg_round<W, PACK>(b->op, nodes, blob, b->nseg_elem, b->div_nseg, t * 32, b->nsegs, lane, h);
+    for (int64_t tt = t; tt < t + k; tt++)
+        seg_round<W, PACK>(b->op, nodes, blob, b->nseg_elem, b->div_nseg, tt * 32, b->nsegs, lane, h);
 }
 
 template <bool PACK>
-__device__ __forceinline__ void serve_tile_dir(const BatchOp *b, int64_t t, int lane, char *scr)
+__device__ __forceinline__ void serve_span_dir(const BatchOp *b, int64_t t, int64_t k, int lane, char *scr, Hint &h)
 {
     switch (b->wsel) {
-    case 0: serve_chunk_tile<16, PACK, true>(b, t, lane, scr); break;
-    case 1: serve_chunk_tile<8, PACK, true>(b, t, lane, scr); break;
-    case 2: serve_chunk_tile<8, PACK, false>(b, t, lane, scr); break;
-    case 3: serve_chunk_tile<4, PACK, true>(b, t, lane, scr); break;
-    case 4: serve_chunk_tile<4, PACK, false>(b, t, lane, scr); break;
-    case 5: serve_chunk_tile<2, PACK, true>(b, t, lane, scr); break;
-    case 6: serve_chunk_tile<2, PACK, false>(b, t, lane, scr); break;
-    case 7: serve_chunk_tile<1, PACK, true>(b, t, lane, scr); break;
-    case 8: serve_chunk_tile<1, PACK, false>(b, t, lane, scr); break;
-    case 9: serve_seg_tile<8, PACK>(b, t, lane); break;
-    case 10: serve_seg_tile<4, PACK>(b, t, lane); break;
-    case 11: serve_seg_tile<2, PACK>(b, t, lane); break;
-    default: serve_seg_tile<1, PACK>(b, t, lane); break;
+    case 0: serve_chunk_span<16, PACK, true>(b, t, k, lane, scr, h); break;
+    case 1: serve_chunk_span<8, PACK, true>(b, t, k, lane, scr, h); break;
+    case 2: serve_chunk_span<8, PACK, false>(b, t, k, lane, scr, h); break;
+    case 3: serve_chunk_span<4, PACK, true>(b, t, k, lane, scr, h); break;
+    case 4: serve_chunk_span<4, PACK, false>(b, t, k, lane, scr, h); break;
+    case 5: serve_chunk_span<2, PACK, true>(b, t, k, lane, scr, h); break;
+    case 6: serve_chunk_span<2, PACK, false>(b, t, k, lane, scr, h); break;
+    case 7: serve_chunk_span<1, PACK, true>(b, t, k, lane, scr, h); break;
+    case 8: serve_chunk_span<1, PACK, false>(b, t, k, lane, scr, h); break;
+    case 9: serve_seg_span<8, PACK>(b, t, k, lane, h); break;
+    case 10: serve_seg_span<4, PACK>(b, t, k, lane, h); break;
+    case 11: serve_seg_span<2, PACK>(b, t, k, lane, h); break;
+    default: serve_seg_span<1, PACK>(b, t, k, lane, h); break;
     }
 }
 
@@ -138,7 +142,12 @@ __device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long
 // slot's previous request completed, so no claimed tile is ever lost.  The
 // host side of the ring (pinned memory) is touched only by the warp that
 // mirrors new requests and by idle warps.
-__global__ void __launch_bounds__(kThreads, 2)
+#ifndef DTE_SERVE_CTAS
+#define DTE_SERVE_CTAS 2
+#endif
+constexpr int kServeCtas = DTE_SERVE_CTAS;  // most CTAs per SM the loop is compiled for
+
+__global__ void __launch_bounds__(kThreads, kServeCtas)
     serve_kernel(const SlotRec *ring, int64_t mask, Ctrl *ctrl, DevState *st, unsigned long long *ctr,
                  unsigned long long *done, SlotRec *dring, int64_t *comp, int64_t span, int64_t idle_budget_ns)
 {
@@ -151,6 +160,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
     int64_t cached = -1;
+    Hint h{-1, 0};  // search position in the current request's descriptor
     int64_t idle_ns = 0;
     unsigned backoff = 256;
     for (;;) {
@@ -185,15 +195,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                     r = tag;
                     k = min(span, nt - t);
                     action = 1;
-                    if (r != cached) {
-                        // the record, read past L1 (a slot is rewritten for each
-                        // request) and after the counter that announced it
-                        const unsigned long long *src = reinterpret_cast<const unsigned long long *>(&dring[slot]);
-                        unsigned long long *dst = reinterpret_cast<unsigned long long *>(&wop[w]);
-                        for (int i = 0; i < (int)(sizeof(BatchOp) / 8); i++) dst[i] = ld_relaxed_gpu(src + i);
-                        wkind[w] = (int32_t)ld_relaxed_gpu(src + sizeof(BatchOp) / 8);
-                        wntiles[w] = nt;
-                    }
+                    wntiles[w] = nt;
                 }
             }
         }
@@ -233,13 +235,25 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
         t = __shfl_sync(FULL, t, 0);
         k = __shfl_sync(FULL, k, 0);
-        __syncwarp();
-        cached = r;
-        const bool pack = wkind[w] == DTE_BATCH_PACK;
-        for (int64_t tt = t; tt < t + k; tt++) {
-            if (pack) serve_tile_dir<true>(&wop[w], tt, lane, scr);
-            else serve_tile_dir<false>(&wop[w], tt, lane, scr);
+        __syncwarp();  // lane 0's fence after the counter orders the other lanes' reads below
+        if (r != cached) {
+            // the request's record, one 8-byte word per lane, read past L1 (a
+            // slot is rewritten for each request) and after the counter that
+            // announced it
+            constexpr int kWords = (int)(sizeof(BatchOp) / 8) + 1;  // the op, then its kind
+            static_assert(kWords <= 32, "record copied one word per lane");
+            const unsigned long long *src = reinterpret_cast<const unsigned long long *>(&dring[r & mask]);
+            if (lane < kWords) {
+                const unsigned long long v = ld_relaxed_gpu(src + lane);
+                if (lane < kWords - 1) reinterpret_cast<unsigned long long *>(&wop[w])[lane] = v;
+                else wkind[w] = (int32_t)v;
+            }
         }
+        __syncwarp();
+        if (r != cached) h = Hint{-1, 0};
+        cached = r;
+        if (wkind[w] == DTE_BATCH_PACK) serve_span_dir<true>(&wop[w], t, k, lane, scr, h);
+        else serve_span_dir<false>(&wop[w], t, k, lane, scr, h);
         __threadfence();
         __syncwarp();
         if (lane == 0) {
@@ -379,7 +393,7 @@ int dte_server_create(const dte_server_config *cfg, dte_server *out)
     dte_server_config c{1024, (int64_t)8 << 30, 2, 4, 50000};
     if (cfg) c = *cfg;
     if (c.ring_slots <= 0 || (c.ring_slots & (c.ring_slots - 1)) || c.ring_slots > (1 << 20)) return DTE_ERR_ARG;
-    if (c.max_inflight_bytes <= 0 || c.ctas_per_sm < 1 || c.ctas_per_sm > 2 || c.span_tiles < 1 ||
+    if (c.max_inflight_bytes <= 0 || c.ctas_per_sm < 1 || c.ctas_per_sm > kServeCtas || c.span_tiles < 1 ||
         c.idle_exit_us < 1)
         return DTE_ERR_ARG;
     int dev = 0;
