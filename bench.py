@@ -576,7 +576,7 @@ def run_config_records(args):
     _line(f"record layout, {nb} indexed blocks ({t.size} B packed)", "pack+unpack GB/s",
           round(4 * t.size / (tp + tu) / 1e9, 1), "GB/s",
           {"pack_GBs": round(2 * t.size / tp / 1e9, 1), "unpack_GBs": round(2 * t.size / tu / 1e9, 1),
-           "descriptor_bytes": None, "iov_device_queries_per_s": round(nq / tq),
+           "descriptor_bytes": t.descriptor_bytes, "iov_device_queries_per_s": round(nq / tq),
            "iov_device_batch_us": round(tq * 1e6, 1),
            "iov_host_query_p50_us": round(float(np.percentile(lat, 50)) * 1e6, 1),
            "iov_host_query_p99_us": round(float(np.percentile(lat, 99)) * 1e6, 1), "hbm_peak_GBs": peak})

@@ -181,6 +181,9 @@ DTE_API int dte_type_get_extent(dte_type type, int64_t *lb, int64_t *extent);
 DTE_API int dte_type_get_true_extent(dte_type type, int64_t *true_lb, int64_t *true_extent);
 /* Number of merged segments of one element (the total of §3.1 iov_len). */
 DTE_API int dte_type_num_segments(dte_type type, int64_t *nseg);
+/* Bytes of the committed device descriptor (one copy per device that used
+ * the type).  DTE_ERR_TYPE if the type is not committed. */
+DTE_API int dte_type_descriptor_bytes(dte_type type, int64_t *bytes);
 
 /* ------------------------------------------------------------------------
  * Segment queries, §3.1.  A segment is a maximal run of typemap entries

@@ -96,6 +96,7 @@ _SIGS = {
     "dte_type_get_extent": ([_p, _pi64, _pi64], C.c_int),
     "dte_type_get_true_extent": ([_p, _pi64, _pi64], C.c_int),
     "dte_type_num_segments": ([_p, _pi64], C.c_int),
+    "dte_type_descriptor_bytes": ([_p, _pi64], C.c_int),
     "dte_type_iov_len": ([_p, _i64, _pi64, _pi64], C.c_int),
     "dte_type_iov": ([_p, _i64, C.POINTER(dte_iov), _i64, _pi64], C.c_int),
     "dte_type_iov_len_async": ([_p, _i64, _p, _p, _p, _p], C.c_int),
@@ -289,6 +290,10 @@ def dte_type_get_true_extent(t: int):
 
 def dte_type_num_segments(t: int) -> int:
     return _q1("dte_type_num_segments", t)
+
+
+def dte_type_descriptor_bytes(t: int) -> int:
+    return _q1("dte_type_descriptor_bytes", t)
 
 
 def dte_type_iov_len(t: int, max_iov_bytes: int):
@@ -537,6 +542,10 @@ class Datatype:
     @property
     def num_segments(self) -> int:
         return dte_type_num_segments(self.h)
+
+    @property
+    def descriptor_bytes(self) -> int:
+        return dte_type_descriptor_bytes(self.h)
 
     def iov_len(self, max_iov_bytes: int):
         return dte_type_iov_len(self.h, max_iov_bytes)

@@ -1181,6 +1181,15 @@ int dte_type_num_segments(dte_type t, int64_t *nseg)
     return DTE_SUCCESS;
 }
 
+int dte_type_descriptor_bytes(dte_type t, int64_t *bytes)
+{
+    if (int rc = check_old(t)) return rc;
+    if (!bytes) return DTE_ERR_ARG;
+    if (!t->committed) return DTE_ERR_TYPE;
+    *bytes = t->desc->bytes;
+    return DTE_SUCCESS;
+}
+
 int dte_type_iov_len(dte_type t, int64_t max_iov_bytes, int64_t *iov_len, int64_t *actual_iov_bytes)
 {
     DTE_TRY

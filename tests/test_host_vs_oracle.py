@@ -214,3 +214,18 @@ def test_range_and_sendrecv_argument_checks():
         dte.dte_sendrecv_enqueue(16, 1, v.h, 16, 1, u.h, 16, 64)
     assert e.value.code == dte.ERR_TYPE
     dte.dte_sendrecv_enqueue(16, 0, u.h, 16, 0, t.h, 16, 64)  # empty message
+
+
+def test_descriptor_sizes_stay_compact():
+    # strided and subarray layouts commit to a few hundred bytes whatever
+    # their size; an index table costs about its entries
+    rng = np.random.default_rng(105)
+    vec = dte.Datatype.vector(1 << 20, 4, 16, dte.FLOAT32).commit()
+    assert vec.descriptor_bytes <= 1024
+    faces = [dte.Datatype.from_spec(f).commit() for f in inputs.halo_face_specs(512, 2)]
+    assert max(f.descriptor_bytes for f in faces) <= 2048
+    rec = dte.Datatype.from_spec(inputs.record_indexed_spec(rng, 1 << 12)).commit()
+    assert 16 * 4096 <= rec.descriptor_bytes <= 64 * 4096
+    with pytest.raises(dte.DteError) as e:
+        dte.Datatype.vector(3, 1, 2, dte.FLOAT32).descriptor_bytes
+    assert e.value.code == dte.ERR_TYPE
