@@ -212,6 +212,8 @@ __global__ void __launch_bounds__(kBulkWarps * 32, 1) bulk_kernel(Desc d, Op op,
     const char *blob;
     const DNode *nodes;
     stage_desc(d, smem, blob, nodes);
+    allow_dependents();
+    prior_grids_wait();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     char *buf = reinterpret_cast<char *>(smem) + buf_off + (int64_t)w * kBulkStages * kBulkTile;
     const uint32_t bar0 = smem_u32(&bars[w][0]);

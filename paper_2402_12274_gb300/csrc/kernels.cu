@@ -59,6 +59,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) move_kernel(Desc d, Op o
     const char *blob;
     const DNode *nodes;
     stage_desc(d, smem, blob, nodes);
+    allow_dependents();
+    prior_grids_wait();
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int64_t nwarps = (int64_t)gridDim.x * kWarps;
@@ -91,6 +93,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) seg_kernel(Desc d, Op op
     const char *blob;
     const DNode *nodes;
     stage_desc(d, smem, blob, nodes);
+    allow_dependents();
+    prior_grids_wait();
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int64_t stride = (int64_t)gridDim.x * kWarps * span;
@@ -127,6 +131,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_kernel(const Batch
         for (int i = threadIdx.x; i < nw; i += blockDim.x) smem[i] = s[i];
         __syncthreads();
     }
+    allow_dependents();
+    prior_grids_wait();
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int64_t nwarps = (int64_t)gridDim.x * kWarps;
@@ -171,6 +177,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_seg_kernel(const B
         for (int i = threadIdx.x; i < nw; i += blockDim.x) smem[i] = s[i];
         __syncthreads();
     }
+    allow_dependents();
+    prior_grids_wait();
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int64_t nwarps = (int64_t)gridDim.x * kWarps;
@@ -505,9 +513,11 @@ static int launch_move(bool pack, dte_type t, const char *dblob, const void *use
         int64_t units = (rounds + span_rounds - 1) / span_rounds;
         int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((units + kWarps - 1) / kWarps,
                                                                 (int64_t)sm_count(dev) * socc));
-        sk<<<(unsigned)blocks, kThreads, smem, stream>>>(d, op, c.nseg, c.nodes()[c.root].div_nseg, seg0, nsegs,
-                                                        32 * span_rounds);
-        if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
+        if (launch_overlapped(sk, (unsigned)blocks, kThreads, smem, stream, d, op, c.nseg,
+                              c.nodes()[c.root].div_nseg, seg0, nsegs, (int64_t)32 * span_rounds) != cudaSuccess) {
+            cudaGetLastError();
+            return DTE_ERR_CUDA;
+        }
         return DTE_SUCCESS;
     }
     if (kBulk && W == 16 && nbytes >= kBulkMinBytes && c.nseg > 0 && c.size / c.nseg >= kBulkMinRun &&
@@ -519,9 +529,11 @@ static int launch_move(bool pack, dte_type t, const char *dblob, const void *use
         const int64_t blocks =
             std::max<int64_t>(1, std::min<int64_t>((ntiles + kBulkWarps - 1) / kBulkWarps, sm_count(dev)));
         auto bk = pack ? bulk_kernel<true> : bulk_kernel<false>;
-        bk<<<(unsigned)blocks, kBulkWarps * 32, (size_t)(buf_off + kBulkSmem), stream>>>(d, op, ntiles,
-                                                                                         (int32_t)buf_off);
-        if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
+        if (launch_overlapped(bk, (unsigned)blocks, kBulkWarps * 32, (size_t)(buf_off + kBulkSmem), stream, d, op,
+                              ntiles, (int32_t)buf_off) != cudaSuccess) {
+            cudaGetLastError();
+            return DTE_ERR_CUDA;
+        }
         return DTE_SUCCESS;
     }
     int64_t nchunks = (op.total + 15) / 16;
@@ -534,9 +546,11 @@ static int launch_move(bool pack, dte_type t, const char *dblob, const void *use
     int64_t units = (steps + span_steps - 1) / span_steps;
     int64_t blocks = std::min<int64_t>((units + kWarps - 1) / kWarps, max_blocks);
     if (blocks < 1) blocks = 1;
-    k<<<(unsigned)blocks, kThreads, smem, stream>>>(d, op, nchunks, span_steps * step,
-                                                    make_spread(units, blocks * kWarps));
-    if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
+    if (launch_overlapped(k, (unsigned)blocks, kThreads, smem, stream, d, op, nchunks, span_steps * step,
+                          make_spread(units, blocks * kWarps)) != cudaSuccess) {
+        cudaGetLastError();
+        return DTE_ERR_CUDA;
+    }
     return DTE_SUCCESS;
 }
 
@@ -950,9 +964,13 @@ int dte_batch_enqueue(dte_batch b, dte_stream_t stream)
         int64_t units = (g.ntiles + span - 1) / span;
         int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((units + kWarps - 1) / kWarps, max_blocks));
         BatchKernel k = b->kind == DTE_BATCH_PACK ? pick_batch<true>(g.wsel) : pick_batch<false>(g.wsel);
-        k<<<(unsigned)blocks, kThreads, (size_t)g.image_bytes, (cudaStream_t)stream>>>(
-            b->d_ops + g.op0, b->d_tile0 + g.t0, g.nops, g.ntiles, span, b->d_image + g.image_off, g.image_bytes,
-            make_spread(units, blocks * kWarps));
+        if (launch_overlapped(k, (unsigned)blocks, kThreads, (size_t)g.image_bytes, (cudaStream_t)stream,
+                              (const BatchOp *)(b->d_ops + g.op0), (const int64_t *)(b->d_tile0 + g.t0), g.nops,
+                              g.ntiles, span, (const char *)(b->d_image + g.image_off), g.image_bytes,
+                              make_spread(units, blocks * kWarps)) != cudaSuccess) {
+            cudaGetLastError();
+            return DTE_ERR_CUDA;
+        }
         if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
     }
     if (capturing(stream)) {

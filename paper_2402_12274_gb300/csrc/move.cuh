@@ -128,6 +128,32 @@ struct Spread {
     int64_t inc;  // (nwarps * mult) mod nspans
 };
 
+// Programmatic dependent launch: the kernels that move user data are
+// launched so that they may start while the previous kernel of the stream
+// drains.  Before the wait a kernel touches only its own descriptor (staged
+// into shared memory); the wait returns once the previous grids have
+// completed and their writes are visible.  Without such a launch both
+// instructions do nothing.
+__device__ __forceinline__ void prior_grids_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_overlapped(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                                     cudaStream_t stream, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Copy an op record (global) into the warp's shared slot; the kernels that
 // walk many ops read the fields from there instead of holding them in
 // registers.  Synchronised on both sides within the warp.
