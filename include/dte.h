@@ -336,7 +336,8 @@ enum dte_batch_kind { DTE_BATCH_UNPACK = 0, DTE_BATCH_PACK = 1 };
 DTE_API int dte_batch_create(int kind, int64_t nops, const dte_op *ops, dte_batch *out);
 
 /* Launch shape of a batch: at most blocks_per_sm CTAs of 256 threads per SM
- * (0 = as many as fit), and span_tiles consecutive 2 KiB tiles taken by a
+ * (0 = as many as fit), and span_tiles consecutive tiles (1 KiB of packed data
+ * for 16-byte copy words, 2 KiB otherwise, or 32-segment rounds) taken by a
  * warp at a time (warps take spans round-robin).  Used by the autotuner;
  * the defaults are (0, 1).  DTE_ERR_ARG for negative/zero values. */
 DTE_API int dte_batch_set_launch(dte_batch batch, int blocks_per_sm, int64_t span_tiles);
@@ -410,7 +411,7 @@ typedef struct dte_server_config {
     int64_t max_inflight_bytes;  /* cap on moved bytes (2*count*size) of admitted, unfinished
                                     requests (default 8 GiB); a larger request is admitted alone */
     int32_t ctas_per_sm;         /* persistent CTAs per SM, 1 or 2 (default 2) */
-    int32_t span_tiles;          /* 2 KiB tiles (or 32-segment rounds) a warp claims at once (4) */
+    int32_t span_tiles;          /* tiles (1-2 KiB, or 32-segment rounds) a warp claims at once (4) */
     int64_t idle_exit_us;        /* empty-poll budget before the loop leaves (default 50000) */
 } dte_server_config;
 
