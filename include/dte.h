@@ -338,7 +338,7 @@ DTE_API int dte_batch_create(int kind, int64_t nops, const dte_op *ops, dte_batc
 /* Launch shape of a batch: at most blocks_per_sm CTAs of 256 threads per SM
  * (0 = as many as fit), and span_tiles consecutive tiles (1 KiB of packed data
  * for 16-byte copy words, 2 KiB otherwise, or 32-segment rounds) taken by a
- * warp at a time (warps take spans round-robin).  Used by the autotuner;
+ * warp at a time (warps take spans in a spread order).  Used by the autotuner;
  * the defaults are (0, 1).  DTE_ERR_ARG for negative/zero values. */
 DTE_API int dte_batch_set_launch(dte_batch batch, int blocks_per_sm, int64_t span_tiles);
 
