@@ -3,8 +3,9 @@
 A batch runs one persistent launch per copy-word class; its shape has two
 knobs (``dte_batch_set_launch``): CTAs per SM and the span of consecutive
 tiles (1-2 KiB of packed data, or 32-segment rounds) a warp takes at a time.
-The best choice depends on the shapes in the batch (many tiny ops favour short spans and full occupancy; long runs
-over large index tables favour longer spans).  The tuner times every
+The best choice depends on the shapes in the batch (many tiny ops favour
+short spans and full occupancy; long runs over large index tables favour
+longer spans).  The tuner times every
 candidate on the batch itself with CUDA events, keeps the fastest, and caches
 it under a signature of the batch's shape mix (per word class: count of ops
 in each power-of-two size bucket), so batches of the same mix reuse it.
