@@ -43,12 +43,17 @@ constexpr int64_t kSmemBlob = 16384;  // stage descriptors up to this size whole
 // Segment-major movement pays off for short runs under a large index table
 // (one direct table lookup per segment instead of a search per run); for
 // strided layouts (divisions only) the chunk-major kernel is faster even
-// with short runs.
-constexpr int64_t kSegMaxRun = 256;
+// with short runs.  Mixed run lengths take it while the mean run is short
+// and no run is long enough to hold a warp's round up for long.
+#ifndef DTE_SEGMAXRUN
+#define DTE_SEGMAXRUN 4096
+#endif
+constexpr int64_t kSegMaxRun = DTE_SEGMAXRUN;   // longest run
+constexpr int64_t kSegMaxMean = 512;            // mean run (size / segments)
 
 static bool use_seg_major(const Committed &c, int W)
 {
-    return W < 16 && c.maxrun <= kSegMaxRun && c.big_list;
+    return W < 16 && c.big_list && c.maxrun <= kSegMaxRun && c.nseg > 0 && c.size / c.nseg <= kSegMaxMean;
 }
 constexpr int kMaxSmemNodes = 64;
 
