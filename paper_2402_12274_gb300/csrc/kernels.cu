@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) move_kernel(Desc d, Op o
     const int64_t warp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int64_t nwarps = (int64_t)gridDim.x * kWarps;
     Hint h{-1, 0};
-    int64_t p = warp < sp.nspans ? (warp * sp.mult) % sp.nspans : 0;
+    int64_t p = spread_first(sp, warp);
     for (int64_t j = warp; j < sp.nspans; j += nwarps) {
         const int64_t c0 = p * span;
         const int64_t c1 = min(c0 + span, nchunks);
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_kernel(const Batch
     Hint oh{-1, 0};
     Hint h{-1, 0};
     int64_t cur = -1;
-    int64_t p = warp < sp.nspans ? (warp * sp.mult) % sp.nspans : 0;
+    int64_t p = spread_first(sp, warp);
     for (int64_t j = warp; j < sp.nspans; j += nwarps, p = p + sp.inc >= sp.nspans ? p + sp.inc - sp.nspans : p + sp.inc) {
         const int64_t s0 = p * span;
         const int64_t s1 = min(s0 + span, ntiles);
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_seg_kernel(const B
     Hint oh{-1, 0};
     Hint h{-1, 0};
     int64_t cur = -1;
-    int64_t p = warp < sp.nspans ? (warp * sp.mult) % sp.nspans : 0;
+    int64_t p = spread_first(sp, warp);
     for (int64_t j = warp; j < sp.nspans; j += nwarps, p = p + sp.inc >= sp.nspans ? p + sp.inc - sp.nspans : p + sp.inc) {
         const int64_t s0 = p * span;
         const int64_t s1 = min(s0 + span, ntiles);

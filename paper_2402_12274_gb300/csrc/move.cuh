@@ -131,7 +131,17 @@ struct Spread {
     int64_t nspans;
     int64_t mult;
     int64_t inc;  // (nwarps * mult) mod nspans
+    FastDiv div;  // / nspans
 };
+
+// The first span warp `warp` takes: (warp * mult) mod nspans, by invariant
+// division (a 64-bit % is a long software routine at the head of every warp).
+__device__ __forceinline__ int64_t spread_first(const Spread &sp, int64_t warp)
+{
+    if (warp >= sp.nspans) return 0;
+    const int64_t x = warp * sp.mult;
+    return x - fdiv(x, sp.div) * sp.nspans;
+}
 
 // Programmatic dependent launch: the kernels that move user data are
 // launched so that they may start while the previous kernel of the stream
@@ -291,6 +301,15 @@ __device__ __forceinline__ void warp_step16(const Op &op, const DNode *nodes, co
     uint4 v[kUOf<16>];
     int64_t d[kUOf<16>];
     int64_t d0 = 0, rem0 = 0;
+    if (!PACK) {
+        // the packed side is addressed by position alone: its loads go out
+        // before the descriptor walks, whose latency they then cover
+#pragma unroll
+        for (int u = 0; u < kUOf<16>; u++) {
+            int64_t c = base + u * 32 + lane;
+            if (c < end) v[u] = __ldg(reinterpret_cast<const uint4 *>(op.packed_in + c * 16));
+        }
+    }
 #pragma unroll
     for (int u = 0; u < kUOf<16>; u++) {
         int64_t c = base + u * 32 + lane;
@@ -306,7 +325,6 @@ __device__ __forceinline__ void warp_step16(const Op &op, const DNode *nodes, co
                 }
             }
             if (PACK) v[u] = __ldg(reinterpret_cast<const uint4 *>(op.user_in + d[u]));
-            else v[u] = __ldg(reinterpret_cast<const uint4 *>(op.packed_in + c * 16));
         }
     }
 #pragma unroll
@@ -541,6 +559,7 @@ static Spread make_spread(int64_t nspans, int64_t nwarps)
         sp.mult = m;
     }
     sp.inc = nspans > 0 ? (int64_t)(((__int128)nwarps * sp.mult) % nspans) : 0;
+    sp.div = make_div(nspans);
     return sp;
 }
 
