@@ -29,7 +29,10 @@ constexpr int64_t kBulkTile = 16384;                 // packed bytes per stage
 constexpr int64_t kBulkSlice = kBulkTile / 32;       // packed bytes per lane of a tile
 constexpr int64_t kBulkSmem = (int64_t)kBulkWarps * kBulkStages * kBulkTile;
 constexpr int64_t kBulkMinRun = 2048;                // mean run length that selects this path
-constexpr int64_t kBulkMinBytes = 1 << 20;           // smallest move that takes this path
+// The path pays off only when every warp of a one-CTA-per-SM grid has several
+// tiles to keep in flight; with one tile per warp, loads and stores serialise
+// and the chunk kernels (a whole move in flight at once) are faster.
+constexpr int64_t kBulkMinTilesPerWarp = 6;
 constexpr long long kBulkWaitCycles = 1ll << 31;     // about one second at 2 GHz
 #ifndef DTE_BULK
 #define DTE_BULK 1

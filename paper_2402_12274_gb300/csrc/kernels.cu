@@ -520,7 +520,8 @@ static int launch_move(bool pack, dte_type t, const char *dblob, const void *use
         }
         return DTE_SUCCESS;
     }
-    if (kBulk && W == 16 && nbytes >= kBulkMinBytes && c.nseg > 0 && c.size / c.nseg >= kBulkMinRun &&
+    if (kBulk && W == 16 && nbytes >= kBulkMinTilesPerWarp * kBulkWarps * kBulkTile * sm_count(dev) &&
+        c.nseg > 0 && c.size / c.nseg >= kBulkMinRun &&
         device_memory(user) && device_memory(packed)) {
         // long runs: bulk copies by the copy engine of each SM (bulk.cuh)
         allow_bulk_smem(dev);

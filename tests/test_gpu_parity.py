@@ -77,18 +77,24 @@ def test_merging_layouts_pack_unpack():
         check_move(inputs.sequential_spec(rng), int(rng.integers(1, 4)), rng)
 
 
+BULK_MOVE = 72 << 20  # well above the size that gives every warp of the bulk grid six tiles
+
+
 @pytest.mark.parametrize("L", [2048, 4096 + 16, 65536, 1 << 20])
 def test_long_runs_take_bulk_copies(L):
     # runs of L bytes (16-byte multiples, 16-byte aligned buffers) in moves of
-    # at least 1 MiB go through the bulk-copy kernels; no bounded wait gives up
+    # BULK_MOVE bytes and more go through the bulk-copy kernels, ragged tile
+    # at the end included; no bounded wait gives up
     rng = np.random.default_rng(210)
-    n = max(2, (3 << 20) // L)
+    n = BULK_MOVE // L + 3
     spec = ("hvector", n, 1, L + 768, ("contig", L // 8, ("basic", "float64")))
-    for count in (1, 2):
-        check_move(spec, count, rng, misalign=False)
+    check_move(spec, 1, rng, misalign=False)
+    if L == 65536:
+        half = ("hvector", n // 2 + 1, 1, L + 768, ("contig", L // 8, ("basic", "float64")))
+        check_move(half, 2, rng, misalign=False)
     # a struct of long and short runs still averages long runs per segment
-    spec = ("struct", [1, 1], [0, 8 << 20], [("contig", (6 << 20) // 8, ("basic", "float64")),
-                                              ("vector", 64, 2, 4, ("basic", "float64"))])
+    spec = ("struct", [1, 1], [0, BULK_MOVE + (8 << 20)],
+            [("contig", BULK_MOVE // 8, ("basic", "float64")), ("vector", 64, 2, 4, ("basic", "float64"))])
     check_move(spec, 1, rng, misalign=False)
     assert dte.dte_device_timeouts() == 0
 

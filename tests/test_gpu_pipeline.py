@@ -87,10 +87,10 @@ def test_range_moves_short_runs_under_index_tables(el):
 
 
 def test_range_moves_long_runs_bulk_copies():
-    # 16-byte aligned windows of at least 1 MiB over long runs take the
+    # 16-byte aligned windows of 66 MiB and more over long runs take the
     # bulk-copy kernels; odd windows fall back to the chunk kernels
     rng = np.random.default_rng(308)
-    spec = ("hvector", 40, 1, 96 << 10, ("contig", 8192, ("basic", "float64")))
+    spec = ("hvector", 1200, 1, 96 << 10, ("contig", 8192, ("basic", "float64")))
     t, o = both(spec)
     total = o.size
     lo, hi = span_of(o, 1)
@@ -98,8 +98,9 @@ def test_range_moves_long_runs_bulk_copies():
     d_src = torch.from_numpy(src).to(DEV)
     full = o.pack(src, 1)
     s = torch.cuda.current_stream()
-    for a, n in ((0, total), (16 * 4097, 1 << 20), (16 * 12345, total - 16 * 12345 - 16 * 77),
-                 (4096, (1 << 20) + 16), (8, 1 << 20)):
+    big = 66 << 20
+    for a, n in ((0, total), (16 * 4097, big), (16 * 12345, total - 16 * 12345 - 16 * 77),
+                 (4096, big + 16), (8, big)):
         out = torch.full((n + 16,), SENT, dtype=torch.uint8, device=DEV)
         dte.pack_range(d_src, 1, t, a, n, out, s)
         got = out.cpu().numpy()
