@@ -395,6 +395,16 @@ __device__ __forceinline__ void seg_round(const Op &op, const DNode *nodes, cons
     const int64_t nwords = (p1 - p0) / W;
     const char *pk_in = op.packed_in - op.pbase;  // indexed by stream offset
     char *pk_out = op.packed_out - op.pbase;
+    // Per lane, once per round: the first word of its segment relative to p0
+    // (lanes past the last segment never start one), and its user
+    // displacement minus its stream offset, so a word's user address is that
+    // of its segment's lane plus the word's own stream offset.
+    const int64_t pw = lane < nvalid ? (ps - p0) / W : INT64_MAX;
+    const int64_t dd = disp - ps;
+    const unsigned upto = 0xffffffffu >> (31 - lane);
+    // segments that start before the current window, minus one (the window
+    // walks forward one 32-word window at a time)
+    int before = __popc(__ballot_sync(FULL, pw < 0)) - 1;
     for (int64_t w0 = 0; w0 < nwords; w0 += 32 * kU) {
         T v[kU];
         int64_t ud[kU];
@@ -403,17 +413,14 @@ __device__ __forceinline__ void seg_round(const Op &op, const DNode *nodes, cons
             // segment of each word of this 32-word window: the segments that
             // start before the window, plus those starting in it up to the
             // word (a bit mask of start positions, one OR-reduction)
-            const int64_t qa = p0 + (w0 + u * 32) * W;
-            const int64_t wi = w0 + u * 32 + lane;
-            const int64_t q = qa + (int64_t)lane * W;
-            const bool valid = lane < nvalid;
-            const int before = __popc(__ballot_sync(FULL, valid && ps < qa)) - 1;
-            const int64_t rel = ps - qa;
-            const unsigned bit = (valid && rel >= 0 && rel < 32 * W) ? 1u << (int)(rel / W) : 0u;
-            const unsigned starts = __reduce_or_sync(FULL, bit);
-            const int lo = before + __popc(starts & (0xffffffffu >> (31 - lane)));
-            ud[u] = __shfl_sync(FULL, disp, lo) + (q - __shfl_sync(FULL, ps, lo));
-            if (wi < nwords) {
+            const int64_t wb = w0 + u * 32;
+            const int64_t rw = pw - wb;
+            const unsigned starts = __reduce_or_sync(FULL, (uint64_t)rw < 32 ? 1u << (int)rw : 0u);
+            const int lo = before + __popc(starts & upto);
+            before += __popc(starts);
+            const int64_t q = p0 + (wb + lane) * W;
+            ud[u] = __shfl_sync(FULL, dd, lo) + q;
+            if (wb + lane < nwords) {
                 if (PACK) v[u] = ldw<W>(op.user_in + ud[u]);
                 else v[u] = ldw<W>(pk_in + q);
             }
