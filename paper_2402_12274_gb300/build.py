@@ -1,7 +1,7 @@
 """Build the in-tree shared library ``libdte.so`` (sm_103a) with nvcc.
 
 Each translation unit is compiled in parallel, then linked with the CUDA
-runtime linked statically so the library only needs the driver at run time.
+runtime linked statically so the library only needs the CUDA driver at run time.
 """
 from __future__ import annotations
 
