@@ -540,7 +540,8 @@ def run_config_vector(args):
 def run_config_records(args):
     """struct{int32[3],float64[5]} resized to 64 B inside an indexed type of
     2^22 geometric blocks: pack/unpack GB/s, device iov chunk lookups from
-    random byte offsets (4096 segments each), host query latency."""
+    random byte offsets (4096 segments each), the full sequential segment
+    list on the device, host query latency."""
     import torch
     import paper_2402_12274_gb300 as dte
     from paper_2402_12274_gb300 import inputs
@@ -562,6 +563,11 @@ def run_config_records(args):
     act = torch.empty(nq, dtype=torch.int64, device=dev)
     tq = _mean_s(s, lambda: dte.dte_type_iov_at_bytes_async(t.h, nq, offs.data_ptr(), m, iov.data_ptr(), first.data_ptr(),
                                                            act.data_ptr(), 0, s.cuda_stream), 10)
+    # the full sequential segment list (16 B written per segment)
+    nseg = t.num_segments
+    full = torch.empty((nseg, 2), dtype=torch.int64, device=dev)
+    tl = _mean_s(s, lambda: dte.dte_type_iov_async(t.h, 1, 0, full.data_ptr(), nseg, 0, 0, s.cuda_stream), 5)
+    del full
     # host queries (the paper's synchronous API): iov_len(B) then iov(k, 4096)
     import ctypes
     buf = (dte.dte_iov * m)()
@@ -577,7 +583,8 @@ def run_config_records(args):
           round(4 * t.size / (tp + tu) / 1e9, 1), "GB/s",
           {"pack_GBs": round(2 * t.size / tp / 1e9, 1), "unpack_GBs": round(2 * t.size / tu / 1e9, 1),
            "descriptor_bytes": t.descriptor_bytes, "iov_device_queries_per_s": round(nq / tq),
-           "iov_device_batch_us": round(tq * 1e6, 1),
+           "iov_device_batch_us": round(tq * 1e6, 1), "iov_full_list_segments": nseg,
+           "iov_full_list_ms": round(tl * 1e3, 3), "iov_full_list_GBs_written": round(16 * nseg / tl / 1e9, 1),
            "iov_host_query_p50_us": round(float(np.percentile(lat, 50)) * 1e6, 1),
            "iov_host_query_p99_us": round(float(np.percentile(lat, 99)) * 1e6, 1), "hbm_peak_GBs": peak})
 

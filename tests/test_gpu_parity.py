@@ -290,7 +290,7 @@ def test_halo_faces_full_size():
     check_halo(512)
 
 
-@pytest.mark.parametrize("nblocks", [1 << 12, 1 << 16])
+@pytest.mark.parametrize("nblocks", [1 << 12, 1 << 16, 1 << 19])
 def test_record_indexed_workload(nblocks):
     check_record_indexed(nblocks)
 
