@@ -65,13 +65,41 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def _code_only(src: str) -> str:
+    """C/C++/CUDA source with comments removed and whitespace runs collapsed
+    (string and character literals kept verbatim), so that the kernel-source
+    hash changes with the code and not with its comments."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def csrc_hash():
+    """Hash of the kernel sources (code only), recorded beside committed ncu
+    figures so that they are used only while the kernels are unchanged."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2402_12274_gb300", "csrc")
     for name in sorted(os.listdir(d)):
-        with open(os.path.join(d, name), "rb") as f:
+        with open(os.path.join(d, name), encoding="utf-8") as f:
             h.update(name.encode())
-            h.update(f.read())
+            h.update(_code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -7,11 +7,12 @@
 //
 // Data movement design (pure data movement, no tensor cores):
 //  * The packed side is contiguous, so work is split in packed space into
-//    2 KiB warp steps; lane l of the warp handles chunks l, l+32, l+64, l+96
-//    (16 bytes each) of a step, so every packed-side access of a warp is one
-//    coalesced 512-byte transaction, and four independent 16-byte loads per
-//    lane are in flight before the stores.  Warps take spans of steps in a
-//    spread order (Spread, move.cuh).
+//    warp steps of 16-byte chunks: 1 KiB for 16-byte copy words (lane l
+//    handles chunks l and l+32), 2 KiB otherwise (chunks l, l+32, l+64,
+//    l+96).  Every packed-side access of a warp is one coalesced 512-byte
+//    transaction, and all of a lane's loads are in flight before its stores
+//    (an unpack issues its packed loads before walking the descriptor).
+//    Warps take spans of steps in a spread order (Spread, move.cuh).
 //  * Each chunk maps back to the user layout through the committed descriptor
 //    (desc.h: REG levels by fast invariant division, LIST levels by a search
 //    that gallops from the step's previous position).  Descriptors of up to
@@ -23,11 +24,14 @@
 //    load and one 16-byte store.  Smaller W assembles the chunk run by run
 //    from W-byte words.
 //  * Short runs under large index tables move segment-major (seg_kernel);
-//    long runs with W = 16 move by TMA bulk copies (bulk_kernel, bulk.cuh).
+//    long runs with W = 16 in moves large enough to give every warp of the
+//    bulk grid several 16 KiB tiles move by TMA bulk copies (bulk_kernel,
+//    bulk.cuh).
 //  * Bytes are moved verbatim through integer registers: no value is ever
 //    converted, so NaN payloads survive.
 //  * Batches: many independent operations (different types, buffers and
-//    sizes) run in one persistent launch over a global list of 2 KiB tiles;
+//    sizes) run in one persistent launch over a global list of tiles (warp
+//    steps, or rounds of 32 segments);
 //    the launch reads only a device-resident op table, so it can be captured
 //    in a CUDA graph and replayed.
 #include <cuda_runtime.h>
@@ -111,7 +115,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) seg_kernel(Desc d, Op op
 // ---------------------------------------------------------------------------
 // One launch per copy-word class present in a batch: ops are grouped by
 // (W, packed side 16-aligned) so each kernel is specialised like move_kernel.
-// tile0: nops+1 prefix of 2 KiB tiles per op of the group.  Warps take spans
+// tile0: nops+1 prefix of the tiles (warp steps) per op of the group.  Warps take spans
 // of `span` consecutive tiles in the spread order.  When the group's descriptors fit
 // in shared memory together (`image`, image_bytes > 0) they are staged once
 // per CTA and every op with soff >= 0 walks its staged copy.

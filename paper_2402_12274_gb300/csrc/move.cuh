@@ -590,8 +590,8 @@ static int prep(dte_type t, dte_stream_t stream, const char **blob, int *dev)
     return device_blob(t, blob, dev);
 }
 
-// Fill one op record: copy word, kernel variant (segment-major for short
-// runs moved in sub-16-byte words, as for single ops) and its work size.
+// Fill one op record: copy word, kernel variant (segment-major by the same
+// rule as single ops) and its work size.
 static void fill_batch_op(BatchOp &h, const Committed &c, int64_t extent, const dte_op &o, const char *dblob)
 {
     size_t smem;
@@ -610,7 +610,8 @@ static void fill_batch_op(BatchOp &h, const Committed &c, int64_t extent, const 
     }
 }
 
-// tiles of an op: 2 KiB steps (chunk-major) or rounds of 32 segments
+// tiles of an op: warp steps (1 KiB for 16-byte words, 2 KiB otherwise) or
+// rounds of 32 segments
 static int64_t op_tiles(const BatchOp &h)
 {
     if (h.wsel >= 9) return (h.nsegs + 31) / 32;
