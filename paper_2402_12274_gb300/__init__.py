@@ -637,6 +637,21 @@ def _ptr_nbytes(x):
     return x.data_ptr(), x.numel() * x.element_size()
 
 
+def _check_span(what: str, nbytes: int, offset: int, count: int, dtype: "Datatype") -> None:
+    """`count` elements of `dtype` with displacement 0 at byte `offset` of a
+    buffer of `nbytes` bytes must touch only bytes inside it: the kernels
+    take raw pointers and cannot check.  Raises ValueError before anything
+    is enqueued."""
+    if count <= 0 or dtype.size == 0:
+        return
+    ends = (0, (count - 1) * dtype.extent)
+    lo = offset + min(ends) + dtype.true_lb
+    hi = offset + max(ends) + dtype.true_lb + dtype.true_extent
+    if lo < 0 or hi > nbytes:
+        raise ValueError(f"{what}: {count} element(s) of the layout touch bytes [{lo}, {hi}) "
+                         f"of a {nbytes}-byte buffer")
+
+
 def _stream_handle(stream):
     if stream is None:
         import torch
@@ -650,8 +665,9 @@ def pack(src, count: int, dtype: Datatype, dst, position: int = 0, stream=None, 
     """Enqueue a pack of `count` elements of `dtype` whose displacement 0 is
     src + src_offset bytes, into dst at byte `position`.  Returns the new
     position."""
-    sp, _ = _ptr_nbytes(src)
+    sp, sn = _ptr_nbytes(src)
     dp, dn = _ptr_nbytes(dst)
+    _check_span("pack source", sn, src_offset, count, dtype)
     return dte_pack_enqueue(sp + src_offset, count, dtype.h, dp, dn, position, _stream_handle(stream))
 
 
@@ -660,7 +676,8 @@ def unpack(src, position: int, dst, count: int, dtype: Datatype, stream=None, ds
     `dtype` whose displacement 0 is dst + dst_offset bytes.  Returns the new
     position."""
     sp, sn = _ptr_nbytes(src)
-    dp, _ = _ptr_nbytes(dst)
+    dp, dn = _ptr_nbytes(dst)
+    _check_span("unpack destination", dn, dst_offset, count, dtype)
     return dte_unpack_enqueue(sp, sn, position, dp + dst_offset, count, dtype.h, _stream_handle(stream))
 
 
@@ -668,10 +685,11 @@ def pack_range(src, count: int, dtype: Datatype, first: int, nbytes: int, dst, s
                src_offset: int = 0, dst_offset: int = 0) -> None:
     """Enqueue packed-stream bytes [first, first + nbytes) of `count` elements
     (displacement 0 at src + src_offset) into dst + dst_offset."""
-    sp, _ = _ptr_nbytes(src)
+    sp, sn = _ptr_nbytes(src)
     dp, dn = _ptr_nbytes(dst)
     if dst_offset < 0 or dst_offset + nbytes > dn:
         raise ValueError("pack_range: destination too small")
+    _check_span("pack_range source", sn, src_offset, count, dtype)
     dte_pack_range_enqueue(sp + src_offset, count, dtype.h, first, nbytes, dp + dst_offset,
                            _stream_handle(stream))
 
@@ -681,9 +699,10 @@ def unpack_range(src, first: int, nbytes: int, dst, count: int, dtype: Datatype,
     """Enqueue the unpack of packed-stream bytes [first, first + nbytes), read
     from src + src_offset, into `count` elements at dst + dst_offset."""
     sp, sn = _ptr_nbytes(src)
-    dp, _ = _ptr_nbytes(dst)
+    dp, dn = _ptr_nbytes(dst)
     if src_offset < 0 or src_offset + nbytes > sn:
         raise ValueError("unpack_range: source too small")
+    _check_span("unpack_range destination", dn, dst_offset, count, dtype)
     dte_unpack_range_enqueue(sp + src_offset, first, nbytes, dp + dst_offset, count, dtype.h,
                              _stream_handle(stream))
 
@@ -692,8 +711,10 @@ def sendrecv(send, sendcount: int, sendtype: Datatype, recv, recvcount: int, rec
              stream=None, send_offset: int = 0, recv_offset: int = 0) -> None:
     """Enqueue the windowed send-to-self pipeline (pack -> copy -> unpack per
     window) from `send` to `recv` through the device buffer `staging`."""
-    sp, _ = _ptr_nbytes(send)
-    rp, _ = _ptr_nbytes(recv)
+    sp, sn = _ptr_nbytes(send)
+    rp, rn = _ptr_nbytes(recv)
     gp, gn = _ptr_nbytes(staging)
+    _check_span("sendrecv send buffer", sn, send_offset, sendcount, sendtype)
+    _check_span("sendrecv receive buffer", rn, recv_offset, recvcount, recvtype)
     dte_sendrecv_enqueue(sp + send_offset, sendcount, sendtype.h, rp + recv_offset, recvcount, recvtype.h,
                          gp, gn, _stream_handle(stream))

@@ -13,7 +13,7 @@ from __future__ import annotations
 
 import torch
 
-from . import Datatype, dte_pack_adjoint_f32_enqueue, dte_pack_enqueue
+from . import Datatype, _check_span, dte_pack_adjoint_f32_enqueue, dte_pack_enqueue
 
 
 class TypedPack(torch.autograd.Function):
@@ -21,6 +21,7 @@ class TypedPack(torch.autograd.Function):
     def forward(ctx, x: torch.Tensor, dtype: Datatype, count: int, offset: int):
         if x.dtype != torch.float32 or not x.is_cuda or not x.is_contiguous():
             raise TypeError("typed_pack expects a contiguous float32 CUDA tensor")
+        _check_span("typed_pack input", 4 * x.numel(), 4 * offset, count, dtype)
         n = count * dtype.size // 4
         out = torch.empty(n, dtype=torch.float32, device=x.device)
         stream = torch.cuda.current_stream(x.device).cuda_stream
