@@ -236,6 +236,17 @@ def job_throughput(bytes_per_rank: float, world: int, seconds: float) -> float:
     return bytes_per_rank * world / seconds / 1e9
 
 
+L2_NOTE = ("GPU arm: L2 flushed between timed steps outside the timed events (512 MiB write, then "
+           "512 MiB read); CPU arm: no cache control")
+
+
+def bench_config(packed_bytes: int, world: int) -> dict:
+    """The workload description both arms print (identical dicts)."""
+    return {"workload": WORKLOAD, "packed_bytes": int(packed_bytes),
+            "alg_bytes_per_step": int(2 * ALG_FACTOR * packed_bytes), "l2": L2_NOTE,
+            "parallelism": f"replicas x{world}"}
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -251,7 +262,7 @@ def oracle_steps(seconds_budget: float, max_steps: int | None = None, warmup: in
     steps; stops after max_steps steps or once the budget is spent.
     Returns (GB/s, steps, secs)."""
     import oracle
-    from paper_2402_12274_gb300 import inputs
+    import inputs
     faces = [oracle.from_spec(f) for f in inputs.halo_face_specs(N, G)]
     send = oracle.from_spec(inputs.all_faces_struct(inputs.halo_face_specs(N, G)))
     grid = np.zeros(N ** 3, np.float64)
@@ -276,7 +287,7 @@ def oracle_steps(seconds_budget: float, max_steps: int | None = None, warmup: in
         if (max_steps and steps >= max_steps) or (seconds_budget and el >= seconds_budget):
             break
     alg = 2 * ALG_FACTOR * size * steps
-    return alg / el / 1e9, steps, el
+    return alg / el / 1e9, steps, el, size
 
 
 def run_reference(args):
@@ -286,12 +297,12 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    gbs, steps, el = oracle_steps(0.0, max_steps=max(1, args.steps), warmup=args.warmup)
+    gbs, steps, el, size = oracle_steps(0.0, max_steps=max(1, args.steps), warmup=args.warmup)
     line = {
         "impl": "reference", "metric": METRIC, "value": round(gbs, 4), "unit": "GB/s", "n_gpus": world,
         "steps": steps, "warmup": args.warmup, "ms_per_step": round(1e3 * el / steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": f"{steps} full steps"},
+        "config": bench_config(size, world),
         "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
                          "sample": f"{steps} full pack+unpack steps after {args.warmup} untimed, single thread"},
         "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -307,7 +318,7 @@ def run_dte(args):
     import torch.distributed as dist
 
     import paper_2402_12274_gb300 as dte
-    from paper_2402_12274_gb300 import inputs
+    import inputs
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -440,7 +451,7 @@ def run_dte(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        gbs, st, el = oracle_steps(12.0)
+        gbs, st, el, _ = oracle_steps(12.0)
         cpu = {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": f"{st} full pack+unpack steps of the same workload, {el:.1f} s, single thread"}
 
@@ -449,9 +460,7 @@ def run_dte(args):
             "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": K,
             "warmup": max(args.warmup, 3), "ms_per_step": round(1e3 * total / K, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "packed_bytes": size, "alg_bytes_per_step": alg_step,
-                       "l2": "flushed between steps outside the timed events (512 MiB write, then 512 MiB read)",
-                       "parallelism": f"replicas x{world}"},
+            "config": bench_config(size, world),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * K,
             "clocks": clk.summary(), "check": "ok" if ok else "MISMATCH",
         }
@@ -500,7 +509,7 @@ def run_config_vector(args):
     import ctypes
     import torch
     import paper_2402_12274_gb300 as dte
-    from paper_2402_12274_gb300 import inputs
+    import inputs
     dev = torch.device("cuda", 0)
     s = torch.cuda.Stream()
     sh = s.cuda_stream
@@ -575,7 +584,7 @@ def run_config_records(args):
     list on the device, host query latency."""
     import torch
     import paper_2402_12274_gb300 as dte
-    from paper_2402_12274_gb300 import inputs
+    import inputs
     dev = torch.device("cuda", 0)
     s = torch.cuda.Stream()
     nb = args.records_blocks
@@ -627,7 +636,8 @@ def run_config_batch(args):
     L2 flush needed)."""
     import torch
     import paper_2402_12274_gb300 as dte
-    from paper_2402_12274_gb300 import autotune, inputs
+    import inputs
+    from paper_2402_12274_gb300 import autotune
     dev = torch.device("cuda", 0)
     s = torch.cuda.Stream()
     nops = args.batch_ops
@@ -717,7 +727,7 @@ def run_config_autograd(args):
     and adjoint (deterministic segmented sum) times."""
     import torch
     import paper_2402_12274_gb300 as dte
-    from paper_2402_12274_gb300 import inputs
+    import inputs
     dev = torch.device("cuda", 0)
     s = torch.cuda.Stream()
     rng = np.random.default_rng(5)
@@ -742,7 +752,7 @@ def run_config_serve(args):
     latency = host arrival time to observed completion."""
     import torch
     import paper_2402_12274_gb300 as dte
-    from paper_2402_12274_gb300 import inputs
+    import inputs
     dev = torch.device("cuda", 0)
     rng = np.random.default_rng(5)
     pool = []
@@ -817,7 +827,7 @@ def run_config_pipeline(args):
     256 MiB large-block hvector message, at several staging sizes."""
     import torch
     import paper_2402_12274_gb300 as dte
-    from paper_2402_12274_gb300 import inputs
+    import inputs
     dev = torch.device("cuda", 0)
     s = torch.cuda.Stream()
     fl = L2Flush(dev)
@@ -866,7 +876,7 @@ def run_config_faces(args):
     runs and the two faces normal to the fastest axis (16-byte runs)."""
     import torch
     import paper_2402_12274_gb300 as dte
-    from paper_2402_12274_gb300 import inputs
+    import inputs
     dev = torch.device("cuda", 0)
     s = torch.cuda.Stream()
     fl = L2Flush(dev)

@@ -161,23 +161,40 @@ DTE_API int dte_type_resized(dte_type old, int64_t lb, int64_t extent, dte_type 
 /* A new handle for the same type (committed if old is). */
 DTE_API int dte_type_dup(dte_type old, dte_type *out);
 
-/* Commit: lower the type into its device descriptor (merged contiguous runs,
- * per-level counts and strides, index tables with prefix sums) and upload it
- * to the current CUDA device when one exists (other devices are uploaded on
- * first use).  Required before any query or data movement.  Idempotent. */
+/* Commit (MPI_Type_commit, which the paper's §3.2 example calls before its
+ * iov queries; §3 notes that a type describes its layout in O(1) where an
+ * explicit iovec list costs one entry per segment): lower the type into its
+ * device descriptor (merged contiguous runs, per-level counts and strides,
+ * index tables with prefix sums) and upload it to the current CUDA device
+ * when one exists (other devices are uploaded on first use).  *type is the
+ * handle to commit (unchanged on return).  Required before any query or data
+ * movement.  Idempotent.  DTE_ERR_ARG for a NULL pointer, DTE_ERR_TYPE for an
+ * invalid handle, DTE_ERR_NOMEM / DTE_ERR_CUDA if the upload fails. */
 DTE_API int dte_type_commit(dte_type *type);
 
-/* Release a handle and set *type = NULL.  Device memory of the descriptor
- * is kept until every operation enqueued with the type has completed
- * (checked with CUDA events); for a type used inside CUDA graph capture it
- * is kept until process exit.  Freeing a predefined handle is DTE_ERR_TYPE. */
+/* Release a handle and set *type = NULL (MPI_Type_free, the last call of the
+ * §3.2 example; under §5's stream-enqueue semantics a free must not cut short
+ * work already queued on a stream).  Device memory of the descriptor is kept
+ * until every operation enqueued with the type has completed (checked with
+ * CUDA events); for a type used inside CUDA graph capture it is kept until
+ * process exit.  Freeing a predefined handle is DTE_ERR_TYPE; a NULL pointer
+ * is DTE_ERR_ARG. */
 DTE_API int dte_type_free(dte_type *type);
 
 /* ------------------------------------------------------------------------
- * Attributes (committed or not).
+ * Attributes (committed or not).  §3.1 defines the iov queries in terms of
+ * a type's bytes (iov_len counts segment bytes up to the type's size), and
+ * the typemap bounds that place consecutive elements come from the MPI
+ * constructor rules the paper builds on (§3).  Each call writes host int64
+ * out-parameters; DTE_ERR_ARG for NULL out-pointers, DTE_ERR_TYPE for an
+ * invalid handle.
  * ------------------------------------------------------------------------ */
+/* Bytes of data in one element (sum of its typemap entries' sizes). */
 DTE_API int dte_type_size(dte_type type, int64_t *size);
+/* lb and extent = ub - lb: element e of a count starts at e*extent. */
 DTE_API int dte_type_get_extent(dte_type type, int64_t *lb, int64_t *extent);
+/* Lowest byte touched and the span up to one past the highest, ignoring
+ * explicit (resized/subarray) bounds. */
 DTE_API int dte_type_get_true_extent(dte_type type, int64_t *true_lb, int64_t *true_extent);
 /* Number of merged segments of one element (the total of §3.1 iov_len). */
 DTE_API int dte_type_num_segments(dte_type type, int64_t *nseg);
@@ -374,6 +391,12 @@ DTE_API int dte_unpack_batch_enqueue(int64_t nops, const dte_op *ops, dte_stream
  *     gives DTE_ERR_TYPE instead of an upload);
  *   - the first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) and should come before any stream capture;
+ *   - a call made while `stream` is being captured returns
+ *     DTE_ERR_UNSUPPORTED and queues nothing: the table is copied from a host
+ *     array that the next call rewrites, so a recorded copy would later read
+ *     the wrong table;
+ *   - devices 0..63 only (the per-device address cache has 64 entries); a
+ *     higher device index gives DTE_ERR_UNSUPPORTED;
  *   - all calls on a device share the array and it keeps the last call's
  *     table: two calls whose work overlaps on the GPU (different streams, or
  *     a call issued before the previous one's kernels have read their table)

@@ -1205,6 +1205,10 @@ extern "C" int dte_pack_batch_enqueue_noalloc(int64_t nops, const dte_op *ops, d
     try {
         if (nops < 0 || (nops > 0 && !ops)) return DTE_ERR_ARG;
         if (nops > kNoAllocMaxOps) return DTE_ERR_UNSUPPORTED;
+        // the op table is copied from a host array that the next call
+        // rewrites, so a copy recorded now and replayed later would read the
+        // wrong table: refuse before anything is queued
+        if (capturing(stream)) return DTE_ERR_UNSUPPORTED;
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) {
             cudaGetLastError();

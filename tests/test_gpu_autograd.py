@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_2402_12274_gb300 import inputs
+import inputs
 
 torch = pytest.importorskip("torch")
 import paper_2402_12274_gb300 as dte  # noqa: E402

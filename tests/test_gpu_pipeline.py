@@ -4,7 +4,7 @@ byte for byte against the oracle's range pack / unpack."""
 import numpy as np
 import pytest
 
-from paper_2402_12274_gb300 import inputs
+import inputs
 from tests.helpers import both, span_of
 
 torch = pytest.importorskip("torch")

@@ -1,15 +1,16 @@
 """The device-resident request loop: requests of mixed sizes and directions
 that arrive while others run are admitted and batched continuously; each
 result must be byte-identical whether the request ran alone or in the mix,
-and identical to the per-call enqueue path (itself checked against the
-oracle).  Also: admission under a small byte cap, leaving when idle and
-relaunching, and argument errors."""
+and identical to the oracle's pack or unpack of the same seeded bytes (into
+a sentinel-filled destination for unpacks).  Also: admission under a small
+byte cap, leaving when idle and relaunching, and argument errors."""
 import time
 
 import numpy as np
 import pytest
 
-from paper_2402_12274_gb300 import inputs
+import inputs
+import oracle
 
 torch = pytest.importorskip("torch")
 import paper_2402_12274_gb300 as dte  # noqa: E402
@@ -27,7 +28,7 @@ def make_requests(rng, n, lo=1 << 10, hi=1 << 20):
         span = t.true_lb + t.true_extent
         user = rng.integers(0, 256, span, dtype=np.uint8)
         packed = rng.integers(0, 256, t.size, dtype=np.uint8)
-        reqs.append(dict(t=t, kind=kind, user=user, packed=packed))
+        reqs.append(dict(t=t, kind=kind, user=user, packed=packed, spec=spec))
     return reqs
 
 
@@ -51,14 +52,19 @@ def outputs(reqs, bufs):
 
 
 def reference(reqs):
-    bufs = buffers(reqs)
-    s = torch.cuda.current_stream()
-    for r, (u, p) in zip(reqs, bufs):
+    """Expected output of every request from the oracle: the packed bytes of
+    a pack, the sentinel-filled user span after an unpack."""
+    out = []
+    for r in reqs:
+        o = oracle.from_spec(r["spec"])
+        assert o.size == r["t"].size
         if r["kind"] == dte.BATCH_PACK:
-            dte.pack(u, 1, r["t"], p, 0, s)
+            out.append(o.pack(r["user"], 1))
         else:
-            dte.unpack(p, 0, u, 1, r["t"], s)
-    return outputs(reqs, bufs)
+            want = np.full(r["user"].size, SENT, np.uint8)
+            o.unpack(r["packed"], 1, want)
+            out.append(want)
+    return out
 
 
 def test_results_identical_alone_and_in_the_mix():

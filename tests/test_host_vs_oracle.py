@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 import paper_2402_12274_gb300 as dte
-from paper_2402_12274_gb300 import inputs
+import inputs
 from tests.helpers import both, iov_arrays
 
 HDR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "dte.h")

@@ -6,7 +6,7 @@ pure function of its seed."""
 import numpy as np
 
 import oracle
-from paper_2402_12274_gb300 import inputs
+import inputs
 
 
 def test_record_layout_recipe():

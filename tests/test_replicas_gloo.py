@@ -18,7 +18,7 @@ def _rank_main(rank, world, port, q):
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     import bench
-    from paper_2402_12274_gb300 import inputs
+    import inputs
     # each replica works on its own seeded shard of the same workload shape
     spec = inputs.strided_vector_spec(64, 4, 16)
     t = oracle.from_spec(spec)

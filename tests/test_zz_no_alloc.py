@@ -7,14 +7,18 @@ library instead of cudaMalloc'd memory.
 Checked through the C ABI against the allocating dte_pack_batch_enqueue on
 the same ops: byte-identical output (the bar every pack test here uses), on
 two calls in a row with different source bytes, since every call reuses the
-same array.  Collected last so that a stop-at-first-failure run has already
-run everything else; it also passes alone in a fresh process."""
+same array; the second call must leave the device's free memory and torch's
+reserved bytes unchanged.  Also: an op of count 0 writes nothing, an empty
+op list succeeds, an uncommitted type is refused, and a call under stream
+capture is refused before anything is queued.  Collected last so that a
+stop-at-first-failure run has already run everything else; it also passes
+alone in a fresh process."""
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 import paper_2402_12274_gb300 as dte  # noqa: E402
-from paper_2402_12274_gb300 import inputs  # noqa: E402
+import inputs  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -38,6 +42,8 @@ def _cases(rng):
         hi = max(e + t.true_lb + t.true_extent for e in ends)
         shift = int(rng.integers(0, 16))
         out.append((t, count, -lo + shift, hi - lo + shift + 1))
+    # an op with count 0 moves nothing (its packed bytes must stay untouched)
+    out.append((out[0][0], 0, out[0][2], out[0][3]))
     return out
 
 
@@ -61,19 +67,64 @@ def test_noalloc_batch_pack_matches_batch_pack_on_two_calls():
         ops_got = [(t.h, c, x.data_ptr() + base, got.data_ptr() + int(o))
                    for (t, c, base, _), x, o in zip(cases, srcs, offs)]
         dte.dte_pack_batch_enqueue(ops_ref, s.cuda_stream)
+        s.synchronize()
+        if call == 1:
+            # the call itself must not allocate: free device memory and torch's
+            # reserved bytes are the same before and after it has run
+            free0, reserved0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
         dte.dte_pack_batch_enqueue_noalloc(ops_got, s.cuda_stream)
         s.synchronize()
+        if call == 1:
+            assert torch.cuda.mem_get_info()[0] == free0
+            assert torch.cuda.memory_reserved() == reserved0
         r, g = ref.cpu().numpy(), got.cpu().numpy()
         for o, z in zip(offs[:-1], sizes):
             o = int(o)
             assert np.array_equal(g[o:o + z], r[o:o + z])
             assert np.all(g[o + z:o + z + 16] == 0xC3 + call)  # nothing written past each op
+        # the count-0 op's slot keeps the sentinel
+        assert sizes[-1] == 0 and np.all(g[int(offs[-2]):int(offs[-1])] == 0xC3 + call)
 
 
-def test_noalloc_rejects_more_ops_than_its_table_holds():
+def test_noalloc_empty_list_and_refusals():
     t = dte.Datatype.vector(4, 1, 2, dte.FLOAT32).commit()
     buf = torch.zeros(1 << 16, dtype=torch.uint8, device="cuda")
+    dte.dte_pack_batch_enqueue_noalloc([])  # nothing to do: success
     ops = [(t.h, 1, buf.data_ptr(), buf.data_ptr() + 64 * i) for i in range(dte.NOALLOC_MAX_OPS + 1)]
     with pytest.raises(dte.DteError) as e:
         dte.dte_pack_batch_enqueue_noalloc(ops)
     assert e.value.code == dte.ERR_UNSUPPORTED
+    u = dte.Datatype.vector(4, 1, 2, dte.FLOAT32)  # never committed
+    with pytest.raises(dte.DteError) as e:
+        dte.dte_pack_batch_enqueue_noalloc([(u.h, 1, buf.data_ptr(), buf.data_ptr() + 4096)])
+    assert e.value.code == dte.ERR_TYPE
+    with pytest.raises(dte.DteError) as e:
+        dte.dte_pack_batch_enqueue_noalloc([(t.h, -1, buf.data_ptr(), buf.data_ptr() + 4096)])
+    assert e.value.code == dte.ERR_ARG
+    # under stream capture the call is refused and queues nothing
+    g = torch.cuda.CUDAGraph()
+    gs = torch.cuda.Stream()
+    codes = []
+    with torch.cuda.graph(g, stream=gs):
+        try:
+            dte.dte_pack_batch_enqueue_noalloc([(t.h, 1, buf.data_ptr(), buf.data_ptr() + 4096)], gs.cuda_stream)
+        except dte.DteError as err:
+            codes.append(err.code)
+    assert codes == [dte.ERR_UNSUPPORTED]
+
+
+def test_noalloc_rejects_more_ops_than_its_table_holds_and_batch_errors():
+    t = dte.Datatype.vector(4, 1, 2, dte.FLOAT32).commit()
+    buf = torch.zeros(1 << 16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(dte.DteError) as e:
+        dte.dte_batch_create(dte.BATCH_UNPACK, [(t.h, 1, buf.data_ptr(), buf.data_ptr())])
+    assert e.value.code == dte.ERR_OVERLAP
+    u = dte.Datatype.vector(4, 1, 2, dte.FLOAT32)
+    with pytest.raises(dte.DteError) as e:
+        dte.dte_batch_create(dte.BATCH_PACK, [(u.h, 1, buf.data_ptr(), buf.data_ptr())])
+    assert e.value.code == dte.ERR_TYPE
+    with pytest.raises(dte.DteError):
+        dte.dte_batch_create(7, [])
+    b = dte.Batch(dte.BATCH_PACK, [])  # empty batch: enqueue is a no-op
+    b.enqueue()
+    b.free()
