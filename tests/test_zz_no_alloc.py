@@ -111,20 +111,3 @@ def test_noalloc_empty_list_and_refusals():
         except dte.DteError as err:
             codes.append(err.code)
     assert codes == [dte.ERR_UNSUPPORTED]
-
-
-def test_noalloc_rejects_more_ops_than_its_table_holds_and_batch_errors():
-    t = dte.Datatype.vector(4, 1, 2, dte.FLOAT32).commit()
-    buf = torch.zeros(1 << 16, dtype=torch.uint8, device="cuda")
-    with pytest.raises(dte.DteError) as e:
-        dte.dte_batch_create(dte.BATCH_UNPACK, [(t.h, 1, buf.data_ptr(), buf.data_ptr())])
-    assert e.value.code == dte.ERR_OVERLAP
-    u = dte.Datatype.vector(4, 1, 2, dte.FLOAT32)
-    with pytest.raises(dte.DteError) as e:
-        dte.dte_batch_create(dte.BATCH_PACK, [(u.h, 1, buf.data_ptr(), buf.data_ptr())])
-    assert e.value.code == dte.ERR_TYPE
-    with pytest.raises(dte.DteError):
-        dte.dte_batch_create(7, [])
-    b = dte.Batch(dte.BATCH_PACK, [])  # empty batch: enqueue is a no-op
-    b.enqueue()
-    b.free()
