@@ -2,13 +2,18 @@
 
 One step = pack the six send faces (a struct of six subarray types, one
 kernel launch) into one contiguous 24 MiB buffer, then unpack that buffer
-into the same six faces of a second 512^3 grid (one launch per face: the
-faces share edge cells, so together they are an overlapping receive layout,
-while each face alone is not).  Metric:
+into the same six faces of a second 512^3 grid (one batched launch of six
+per-face operations: the faces share edge cells, so together they are an
+overlapping receive layout, while each face alone is not).  Metric:
 algorithmic bytes (read + written user bytes, 2 * packed bytes per pack and
 per unpack) per second.  L2 is flushed between timed steps (a 512 MiB write
-outside the timed events), since the touched bytes would otherwise fit in
-the 126 MB L2.
+and a 512 MiB read outside the timed events), since the touched bytes would
+otherwise fit in the 126 MB L2.
+
+After the timed steps the same line carries the rest of the metric under
+"secondary": the large-block pack gate (fraction of the HBM roofline), the
+10^4-op batch against per-call launches, and the serving loop's p50/p99
+latency and its speedup over per-call launches (--no-secondary skips them).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dte|reference]
 
@@ -48,6 +53,9 @@ def parse():
     p.add_argument("--impl", default="dte", choices=["dte", "reference"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-tune", action="store_true", help="keep the fixed kernel rule (no plan tuning)")
+    p.add_argument("--no-secondary", action="store_true",
+                   help="skip the rest of the metric (large-block gate, batch vs per-call, serving loop)")
     p.add_argument("--config", default="halo",
                    help="halo (headline, default) | vector | records | batch | largeblock | autograd | serve | "
                         "pipeline | faces | all")
@@ -116,6 +124,28 @@ def traffic_from_profile(kernel: str):
     if not ent or ent.get("csrc_hash") != csrc_hash():
         return None
     return ent.get("dram_bytes_per_launch")
+
+
+def sector_floor(faces, grid_bytes: int, packed_bytes: int):
+    """DRAM bytes the six-face step cannot avoid at 32-byte sector
+    granularity, from the faces' segment lists (every run here is a multiple
+    of 16 bytes at a 16-byte boundary): pack reads every user sector a run
+    touches (union over the faces, which share edge cells) and writes the
+    packed bytes; unpack reads the packed bytes, writes every touched sector
+    and first reads back (fills) each sector it writes only in part.
+    Returns {"pack": bytes, "unpack": bytes, "touched_sectors", "partial_sectors"}."""
+    import paper_2402_12274_gb300 as dte
+    units = grid_bytes // 16
+    diff = np.zeros(units + 1, np.int32)
+    for f in faces:
+        lst = np.array(dte.dte_type_iov(f.h, 0, f.num_segments), dtype=np.int64).reshape(-1, 2)
+        np.add.at(diff, lst[:, 0] // 16, 1)
+        np.add.at(diff, (lst[:, 0] + lst[:, 1]) // 16, -1)
+    cov = (np.cumsum(diff[:-1]) > 0).reshape(-1, 2).sum(axis=1)
+    touched = int(np.count_nonzero(cov))
+    partial = int(np.count_nonzero(cov == 1))
+    return {"pack": 32 * touched + packed_bytes, "unpack": packed_bytes + 32 * touched + 32 * partial,
+            "touched_sectors": touched, "partial_sectors": partial}
 
 
 class ClockSampler:
@@ -340,6 +370,22 @@ def run_dte(args):
     sh = stream.cuda_stream
     flush = L2Flush(dev)
 
+    # kernel plans per shape, measured here (setup, before the warm-up): the
+    # six-face pack is one single move, the unpack batch holds three shapes
+    # (faces with 4 MiB, 8 KiB and 16-byte runs)
+    tuner = None
+    if not args.no_tune:
+        from paper_2402_12274_gb300 import autotune
+        with torch.cuda.stream(stream):
+            tuner = {"pack": autotune.tune_plans(dte.BATCH_PACK, [(send.h, 1, grid.data_ptr(), packed.data_ptr())],
+                                                 stream=stream, reps=60, flush=flush.zero_, single=True,
+                                                 use_cache=False),
+                     "unpack_batch": autotune.tune_plans(dte.BATCH_UNPACK,
+                                                         [(f.h, 1, grid2.data_ptr(), packed.data_ptr() + o)
+                                                          for f, o in zip(faces, offs)],
+                                                         stream=stream, reps=60, flush=flush.zero_,
+                                                         use_cache=False)}
+
     # the six faces share edge cells, so they are unpacked as one batch of six
     # per-face operations (one launch); shared cells receive identical bytes
     batches = {}
@@ -443,17 +489,44 @@ def run_dte(args):
     per_launch = size
     achieved = ALG_FACTOR * per_launch / tdom / 1e9
     kname = "dte::move_kernel<16, 1, 1>" if dom == "pack" else "dte::batch_kernel<16, 0, 1>"
+    # the layout's own floor: DRAM bytes at 32-byte sector granularity (the
+    # 16-byte runs of the fastest-axis faces cost a whole sector each, and an
+    # unpack fills every sector it writes in part)
+    floor = sector_floor(faces, N ** 3 * 8, size)
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic_from_profile(kname),
             "kernel": kname, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
             "pack_ms": round(mp * 1e3, 4), "unpack_ms": round(mu * 1e3, 4),
-            "alg_bytes_per_launch": ALG_FACTOR * per_launch}
+            "alg_bytes_per_launch": ALG_FACTOR * per_launch,
+            "floor_bytes": floor[dom], "frac_of_floor": round(floor[dom] / tdom / 1e9 / peak, 4),
+            "floor_bytes_pack": floor["pack"], "floor_bytes_unpack": floor["unpack"],
+            "frac_of_floor_pack": round(floor["pack"] / mp / 1e9 / peak, 4),
+            "frac_of_floor_unpack": round(floor["unpack"] / mu / 1e9 / peak, 4)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         gbs, st, el, _ = oracle_steps(12.0)
         cpu = {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": f"{st} full pack+unpack steps of the same workload, {el:.1f} s, single thread"}
+
+    # the rest of the metric, measured after the timed region: the large-block
+    # pack gate, batched ops/s against per-call launches, and the serving
+    # loop's latency and its speedup over per-call launches (one GPU only)
+    secondary = None
+    if rank == 0 and world == 1 and not args.no_secondary:
+        del flush
+        torch.cuda.empty_cache()
+        secondary = {}
+        for key, fn in (("largeblock_gate", lambda: largeblock_measure()),
+                        ("batch", lambda: batch_measure(args.batch_ops, graphs=False)),
+                        ("serving", lambda: serve_measure(args.serve_requests))):
+            t0 = time.perf_counter()
+            try:
+                secondary[key] = fn()
+            except Exception as exc:  # recorded, the headline line still prints
+                secondary[key] = {"error": f"{type(exc).__name__}: {exc}"}
+            secondary[key]["wall_s"] = round(time.perf_counter() - t0, 1)
+            torch.cuda.empty_cache()
 
     if rank == 0:
         line = {
@@ -463,6 +536,7 @@ def run_dte(args):
             "config": bench_config(size, world),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * K,
             "clocks": clk.summary(), "check": "ok" if ok else "MISMATCH",
+            "tuner": tuner, "secondary": secondary,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -629,18 +703,17 @@ def run_config_records(args):
            "iov_host_query_p99_us": round(float(np.percentile(lat, 99)) * 1e6, 1), "hbm_peak_GBs": peak})
 
 
-def run_config_batch(args):
+def batch_measure(nops: int, graphs: bool = True):
     """10^4 independent packs (vector/indexed/subarray of float32 or bf16,
     64 B - 4 MiB, seed 4): per-call launches vs one autotuned batch, each
-    also replayed from a captured CUDA graph.  Inputs total several GB (no
-    L2 flush needed)."""
+    optionally also replayed from a captured CUDA graph.  Inputs total several
+    GB (no L2 flush needed)."""
     import torch
     import paper_2402_12274_gb300 as dte
-    import inputs
     from paper_2402_12274_gb300 import autotune
+    import inputs
     dev = torch.device("cuda", 0)
     s = torch.cuda.Stream()
-    nops = args.batch_ops
     rng = np.random.default_rng(4)
     specs = inputs.batch_specs(rng, nops)
     types = [dte.Datatype.from_spec(sp).commit() for sp, _ in specs]
@@ -660,7 +733,13 @@ def run_config_batch(args):
         for t, a, b, z in zip(types, so, po, sizes):
             dte.dte_pack_enqueue(src.data_ptr() + int(a), 1, t.h, pk.data_ptr() + int(b), z, 0, sh)
 
+    # the fixed kernel rule, then plans picked per shape group, in one run
+    auto = dte.Batch(dte.BATCH_PACK, ops)
+    t_auto = _mean_s(s, lambda: auto.enqueue(s), 10)
+    auto.free()
+    plans = autotune.tune_plans(dte.BATCH_PACK, ops, stream=s, reps=3, use_cache=False)
     batch = dte.Batch(dte.BATCH_PACK, ops)
+    t_plans = _mean_s(s, lambda: batch.enqueue(s), 10)
     shapes = [(16, z) for z in sizes]
     best, _, table = autotune.tune(batch, dte.BATCH_PACK, shapes, stream=s, reps=3, use_cache=False)
     t_batch = _mean_s(s, lambda: batch.enqueue(s), 10)
@@ -668,36 +747,49 @@ def run_config_batch(args):
     pk.zero_()
     t_call = _mean_s(s, per_call, 3)
     same = bool(torch.equal(pk, pk_b))
-
-    def graph_of(fn):
-        g = torch.cuda.CUDAGraph()
-        gs = torch.cuda.Stream()
-        with torch.cuda.graph(g, stream=gs):
-            fn(gs)
-        return g
-
-    g_batch = graph_of(lambda gs: batch.enqueue(gs))
-    g_call = graph_of(lambda gs: [dte.dte_pack_enqueue(src.data_ptr() + int(a), 1, t.h, pk.data_ptr() + int(b), z, 0,
-                                                       gs.cuda_stream) for t, a, b, z in zip(types, so, po, sizes)])
-    t_gb = _mean_s(s, g_batch.replay, 10)
-    t_gc = _mean_s(s, g_call.replay, 3)
-    peak, _ = peaks()
-    _line(f"{nops} independent packs, 64 B-4 MiB (vector/indexed/subarray, f32/bf16), {total} B packed",
-          "batched pack ops/s", round(nops / t_batch), "ops/s",
-          {"batch_GBs": round(2 * total / t_batch / 1e9, 1), "batch_ms": round(t_batch * 1e3, 3),
+    del pk_b
+    out = {"ops": nops, "packed_bytes": total, "ops_per_s": round(nops / t_batch),
+           "batch_GBs": round(2 * total / t_batch / 1e9, 1), "batch_ms": round(t_batch * 1e3, 3),
            "per_call_ops_per_s": round(nops / t_call), "per_call_ms": round(t_call * 1e3, 3),
-           "graph_batch_ms": round(t_gb * 1e3, 3), "graph_per_call_ms": round(t_gc * 1e3, 3),
            "speedup_batch_vs_per_call": round(t_call / t_batch, 2),
-           "speedup_graph_batch_vs_graph_per_call": round(t_gc / t_gb, 2),
+           "fixed_rule_batch_ms": round(t_auto * 1e3, 3), "tuned_plans_batch_ms": round(t_plans * 1e3, 3),
+           "plan_groups_changed": {k: v for k, v in plans.items()
+                                   if not k.startswith("_") and v["pick"] not in ("auto", v["auto"])},
+           "plan_groups": sum(not k.startswith("_") for k in plans), "plan_totals_ms": plans.get("_total_ms"),
            "autotuned_launch": {"blocks_per_sm": best[0], "span_tiles": best[1]},
            "autotune_table_ms": {f"{b}x{sp}": round(v * 1e3, 3) for (b, sp), v in (table or {}).items()},
-           "bit_identical_batch_vs_per_call": same, "hbm_peak_GBs": peak})
+           "bit_identical_batch_vs_per_call": same}
+    if graphs:
+        def graph_of(fn):
+            g = torch.cuda.CUDAGraph()
+            gs = torch.cuda.Stream()
+            with torch.cuda.graph(g, stream=gs):
+                fn(gs)
+            return g
+
+        g_batch = graph_of(lambda gs: batch.enqueue(gs))
+        g_call = graph_of(lambda gs: [dte.dte_pack_enqueue(src.data_ptr() + int(a), 1, t.h, pk.data_ptr() + int(b),
+                                                           z, 0, gs.cuda_stream)
+                                      for t, a, b, z in zip(types, so, po, sizes)])
+        t_gb = _mean_s(s, g_batch.replay, 10)
+        t_gc = _mean_s(s, g_call.replay, 3)
+        out.update({"graph_batch_ms": round(t_gb * 1e3, 3), "graph_per_call_ms": round(t_gc * 1e3, 3),
+                    "speedup_graph_batch_vs_graph_per_call": round(t_gc / t_gb, 2)})
+    batch.free()
+    return out
 
 
-def run_config_largeblock(args):
+def run_config_batch(args):
+    r = batch_measure(args.batch_ops)
+    peak, _ = peaks()
+    _line(f"{args.batch_ops} independent packs, 64 B-4 MiB (vector/indexed/subarray, f32/bf16), "
+          f"{r['packed_bytes']} B packed", "batched pack ops/s", r["ops_per_s"], "ops/s", dict(hbm_peak_GBs=peak, **r))
+
+
+def largeblock_measure(runs=(1024, 4096, 16384, 65536, 262144, 1 << 20), reps: int = 30):
     """Large-block pack/unpack: hvector of runs of 1 KiB - 1 MiB with gaps of
-    half a run, 256 MiB packed (the HBM-roofline gate), with torch's own
-    device copy of 256 MiB beside it."""
+    half a run, 256 MiB packed (the HBM-roofline gate), L2 flushed between
+    reps, with torch's own device copy of 256 MiB beside it."""
     import torch
     import paper_2402_12274_gb300 as dte
     dev = torch.device("cuda", 0)
@@ -706,19 +798,30 @@ def run_config_largeblock(args):
     dst = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     src = torch.empty((256 << 20) * 3 // 2 + (1 << 20), dtype=torch.uint8, device=dev)
     res = {}
-    for L in (1024, 4096, 16384, 65536, 262144, 1 << 20):
+    for L in runs:
         n = (256 << 20) // L
         t = dte.Datatype.hvector(n, 1, L + L // 2, dte.Datatype.contiguous(L // 8, dte.FLOAT64)).commit()
-        tp = _mean_s(s, lambda: dte.dte_pack_enqueue(src.data_ptr(), 1, t.h, dst.data_ptr(), dst.numel(), 0, s.cuda_stream), 30, fl)
-        tu = _mean_s(s, lambda: dte.dte_unpack_enqueue(dst.data_ptr(), dst.numel(), 0, src.data_ptr(), 1, t.h, s.cuda_stream), 30, fl)
+        tp = _mean_s(s, lambda: dte.dte_pack_enqueue(src.data_ptr(), 1, t.h, dst.data_ptr(), dst.numel(), 0,
+                                                     s.cuda_stream), reps, fl)
+        tu = _mean_s(s, lambda: dte.dte_unpack_enqueue(dst.data_ptr(), dst.numel(), 0, src.data_ptr(), 1, t.h,
+                                                       s.cuda_stream), reps, fl)
         res[str(L)] = {"pack_GBs": round(2 * t.size / tp / 1e9, 1), "unpack_GBs": round(2 * t.size / tu / 1e9, 1)}
-    tc = _mean_s(s, lambda: dst.copy_(src[: 256 << 20]), 30, fl)
+    tc = _mean_s(s, lambda: dst.copy_(src[: 256 << 20]), reps, fl)
     peak, kind = peaks()
-    worst = min(v["pack_GBs"] for v in res.values())
+    wp = min(v["pack_GBs"] for v in res.values())
+    wu = min(v["unpack_GBs"] for v in res.values())
+    del fl, dst, src
+    return {"min_pack_GBs": wp, "min_unpack_GBs": wu, "pack_frac_of_peak": round(wp / peak, 4),
+            "unpack_frac_of_peak": round(wu / peak, 4), "gate": 0.75,
+            "gate_met": bool(wp / peak >= 0.75), "peak": peak, "peak_source": kind, "runs": res,
+            "torch_copy_GBs": round(2 * (256 << 20) / tc / 1e9, 1),
+            "l2": "flushed between reps (write + read 512 MiB)"}
+
+
+def run_config_largeblock(args):
+    r = largeblock_measure()
     _line("large-block hvector sweep, runs 1 KiB-1 MiB, 256 MiB packed", "large-block pack GB/s (min over runs)",
-          worst, "GB/s", {"frac_of_peak": round(worst / peak, 4), "peak": peak, "peak_source": kind,
-                          "runs": res, "torch_copy_GBs": round(2 * (256 << 20) / tc / 1e9, 1),
-                          "l2": "flushed between reps (write + read 512 MiB)"})
+          r["min_pack_GBs"], "GB/s", r)
 
 
 def run_config_autograd(args):
@@ -744,17 +847,20 @@ def run_config_autograd(args):
                                             "backward_us": round(tb * 1e6, 1), "entries": t.size // 4})
 
 
-def run_config_serve(args):
+def serve_measure(nreq: int, rhos=(0.5, 0.8, 0.95), seed: int = 5, ctas_per_sm: int = 2):
     """Request loop under Poisson arrivals: pack/unpack requests (50/50) of
     layouts from the batch generator with sizes log-uniform 1 KiB - 64 MiB,
     admission cap 8 GiB.  The service rate mu is measured first (all requests
-    submitted at once); then arrivals at rho*mu for rho in {0.5, 0.8, 0.95},
-    latency = host arrival time to observed completion."""
+    submitted at once); then arrivals at rho*mu for each rho, latency = host
+    arrival time to observed completion.  Beside it, the same requests as
+    per-call enqueues on one stream (dte_pack_enqueue / dte_unpack_enqueue,
+    wall time from the first enqueue to the stream's completion) and as two
+    plain batches (one pack, one unpack)."""
     import torch
     import paper_2402_12274_gb300 as dte
     import inputs
     dev = torch.device("cuda", 0)
-    rng = np.random.default_rng(5)
+    rng = np.random.default_rng(seed)
     pool = []
     for spec, _ in inputs.batch_specs(rng, 160, lo=1 << 10, hi=64 << 20):
         t = dte.Datatype.from_spec(spec).commit()
@@ -765,11 +871,10 @@ def run_config_serve(args):
         p.random_(0, 256)
         pool.append((t, u, p))
     torch.cuda.synchronize()
-    nreq = args.serve_requests
     picks = rng.integers(0, len(pool), nreq)
     kinds = rng.integers(0, 2, nreq)
     nbytes = np.array([2 * pool[i][0].size for i in picks], dtype=np.float64)
-    srv = dte.dte_server_create(ring_slots=1024, max_inflight_bytes=8 << 30)
+    srv = dte.dte_server_create(ring_slots=1024, max_inflight_bytes=8 << 30, ctas_per_sm=ctas_per_sm)
 
     def submit(i):
         t, u, p = pool[picks[i]]
@@ -786,7 +891,7 @@ def run_config_serve(args):
     t_all = time.perf_counter() - t0
     mu = nreq / t_all
     res = {}
-    for rho in (0.5, 0.8, 0.95):
+    for rho in rhos:
         gaps = rng.exponential(1.0 / (rho * mu), nreq)
         arrive = np.cumsum(gaps)
         lat = np.zeros(nreq)
@@ -812,12 +917,49 @@ def run_config_serve(args):
                          "throughput_GBs": round(float(nbytes.sum()) / wall / 1e9, 1),
                          "offered_req_per_s": round(rho * mu, 1)}
     dte.dte_server_free(srv)
-    _line(f"request loop, {nreq} Poisson-arriving pack/unpack requests of 1 KiB-64 MiB, 8 GiB cap",
-          "p99 latency at rho=0.8 (ms)", res["0.8"]["p99_ms"], "ms",
-          {"higher_is_better": False, "service_rate_req_per_s": round(mu, 1),
-           "host_submit_us_per_request": round(t_sub / nreq * 1e6, 2),
-           "service_GBs": round(float(nbytes.sum()) / t_all / 1e9, 1), "by_load": res,
-           "mean_request_bytes_moved": round(float(nbytes.mean()))})
+    # the same requests launched one by one on one stream
+    s = torch.cuda.Stream()
+    sh = s.cuda_stream
+
+    def per_call():
+        for i in range(nreq):
+            t, u, p = pool[picks[i]]
+            if kinds[i] == dte.BATCH_PACK:
+                dte.dte_pack_enqueue(u.data_ptr(), 1, t.h, p.data_ptr(), t.size, 0, sh)
+            else:
+                dte.dte_unpack_enqueue(p.data_ptr(), t.size, 0, u.data_ptr(), 1, t.h, sh)
+
+    per_call()
+    s.synchronize()
+    t0 = time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    per_call()
+    e1.record(s)
+    s.synchronize()
+    t_call = time.perf_counter() - t0
+    t_call_gpu = e0.elapsed_time(e1) * 1e-3
+    # and as two plain batches
+    ops = {k: [(pool[picks[i]][0].h, 1, pool[picks[i]][1].data_ptr(), pool[picks[i]][2].data_ptr())
+               for i in range(nreq) if kinds[i] == k] for k in (dte.BATCH_PACK, dte.BATCH_UNPACK)}
+    bs = [dte.Batch(k, v) for k, v in ops.items() if v]
+    t_b = _mean_s(s, lambda: [b.enqueue(s) for b in bs], 5)
+    for b in bs:
+        b.free()
+    total = float(nbytes.sum())
+    return {"service_rate_req_per_s": round(mu, 1), "host_submit_us_per_request": round(t_sub / nreq * 1e6, 2),
+            "service_GBs": round(total / t_all / 1e9, 1), "by_load": res,
+            "per_call": {"wall_ms": round(t_call * 1e3, 2), "gpu_ms": round(t_call_gpu * 1e3, 2),
+                         "GBs": round(total / t_call / 1e9, 1)},
+            "speedup_served_vs_per_call": round(t_call / t_all, 2),
+            "two_batches": {"ms": round(t_b * 1e3, 2), "GBs": round(total / t_b / 1e9, 1)},
+            "requests": nreq, "mean_request_bytes_moved": round(float(nbytes.mean()))}
+
+
+def run_config_serve(args):
+    r = serve_measure(args.serve_requests)
+    _line(f"request loop, {args.serve_requests} Poisson-arriving pack/unpack requests of 1 KiB-64 MiB, 8 GiB cap",
+          "p99 latency at rho=0.8 (ms)", r["by_load"]["0.8"]["p99_ms"], "ms", dict(higher_is_better=False, **r))
 
 
 def run_config_pipeline(args):

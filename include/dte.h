@@ -372,6 +372,55 @@ DTE_API int dte_batch_free(dte_batch *batch);
 DTE_API int dte_pack_batch_enqueue(int64_t nops, const dte_op *ops, dte_stream_t stream);
 DTE_API int dte_unpack_batch_enqueue(int64_t nops, const dte_op *ops, dte_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Kernel plans.  The paper's §5 enqueues (buf, count, datatype) operations
+ * and leaves how the datatype engine moves them to the implementation; a
+ * plan picks among this library's ways of moving one type.  A batch or a
+ * single move reads the plan of each operation's type when it is created or
+ * enqueued.  The default, DTE_PLAN_AUTO, is a fixed rule: segment-major for
+ * copy words below 16 bytes with runs of at most 4 KiB and a mean run of at
+ * most 512 bytes under an index list of more than 32 entries; TMA bulk
+ * copies for single moves of runs averaging at least 2 KiB with 16-byte
+ * words between device buffers, large enough to give every warp of a
+ * one-CTA-per-SM grid six 16 KiB tiles; chunk-major otherwise.  An
+ * autotuner that measures layouts of each shape picks a plan per type.  A
+ * plan that does not apply to a move (segment-major with 16-byte words or
+ * runs over 4 KiB, the wide step with smaller words, bulk copies inside
+ * batches or outside device memory) leaves that move to the fixed rule.
+ * ------------------------------------------------------------------------ */
+enum dte_plan {
+    DTE_PLAN_AUTO = 0,        /* the fixed rule above */
+    DTE_PLAN_CHUNK = 1,       /* chunk-major: 16-byte packed chunks, 1 KiB warp steps for 16-byte words */
+    DTE_PLAN_CHUNK_WIDE = 2,  /* chunk-major with 2 KiB warp steps for 16-byte words */
+    DTE_PLAN_SEGMENT = 3,     /* segment-major: rounds of 32 runs, one descriptor walk per run */
+    DTE_PLAN_BULK = 4         /* TMA bulk copies of 16 KiB tiles (single moves between device buffers) */
+};
+
+/* Set the plan of a type handle (any DTE_PLAN_*; DTE_ERR_ARG otherwise;
+ * DTE_ERR_TYPE for a predefined handle).  Affects moves enqueued and
+ * batches created afterwards; dte_type_dup copies it. */
+DTE_API int dte_type_set_plan(dte_type type, int plan);
+DTE_API int dte_type_get_plan(dte_type type, int *plan);
+
+/* The shape of one operation as the kernels see it, for tuners that group
+ * operations by shape. */
+typedef struct dte_op_shape {
+    int32_t word;          /* copy word in bytes: 16, 8, 4, 2 or 1 */
+    int32_t list;          /* 1 if the layout has an index list of more than 32 entries */
+    int32_t single_kernel; /* DTE_PLAN_CHUNK, _CHUNK_WIDE, _SEGMENT or _BULK: what a single move takes now */
+    int32_t batch_kernel;  /* DTE_PLAN_CHUNK, _CHUNK_WIDE or _SEGMENT: what it takes inside a batch */
+    int64_t bytes;         /* packed bytes (count * size) */
+    int64_t segments;      /* runs over the count elements (count * segments of one element) */
+    int64_t max_run;       /* longest run in bytes */
+} dte_op_shape;
+
+/* Describe `op` (a committed type, count, user and packed pointers as in a
+ * batch; the pointers are only inspected, never dereferenced, except that a
+ * bulk-copy decision asks the CUDA runtime whether both are device memory).
+ * DTE_ERR_TYPE for an invalid or uncommitted type, DTE_ERR_ARG for NULL
+ * pointers or a negative count. */
+DTE_API int dte_op_shape_query(const dte_op *op, dte_op_shape *out);
+
 /* Largest nops accepted by dte_pack_batch_enqueue_noalloc. */
 #define DTE_NOALLOC_MAX_OPS 256
 

@@ -56,6 +56,16 @@ class dte_op(C.Structure):
 BATCH_UNPACK, BATCH_PACK = 0, 1
 
 
+class dte_op_shape(C.Structure):
+    _fields_ = [("word", C.c_int32), ("list", C.c_int32), ("single_kernel", C.c_int32),
+                ("batch_kernel", C.c_int32), ("bytes", C.c_int64), ("segments", C.c_int64),
+                ("max_run", C.c_int64)]
+
+
+# kernel plans (include/dte.h, enum dte_plan)
+PLAN_AUTO, PLAN_CHUNK, PLAN_CHUNK_WIDE, PLAN_SEGMENT, PLAN_BULK = range(5)
+
+
 class dte_server_config(C.Structure):
     _fields_ = [("ring_slots", C.c_int64), ("max_inflight_bytes", C.c_int64), ("ctas_per_sm", C.c_int32),
                 ("span_tiles", C.c_int32), ("idle_exit_us", C.c_int64)]
@@ -97,6 +107,9 @@ _SIGS = {
     "dte_type_get_true_extent": ([_p, _pi64, _pi64], C.c_int),
     "dte_type_num_segments": ([_p, _pi64], C.c_int),
     "dte_type_descriptor_bytes": ([_p, _pi64], C.c_int),
+    "dte_type_set_plan": ([_p, C.c_int], C.c_int),
+    "dte_type_get_plan": ([_p, C.POINTER(C.c_int)], C.c_int),
+    "dte_op_shape_query": ([C.POINTER(dte_op), C.POINTER(dte_op_shape)], C.c_int),
     "dte_type_iov_len": ([_p, _i64, _pi64, _pi64], C.c_int),
     "dte_type_iov": ([_p, _i64, C.POINTER(dte_iov), _i64, _pi64], C.c_int),
     "dte_type_iov_len_async": ([_p, _i64, _p, _p, _p, _p], C.c_int),
@@ -294,6 +307,24 @@ def dte_type_num_segments(t: int) -> int:
 
 def dte_type_descriptor_bytes(t: int) -> int:
     return _q1("dte_type_descriptor_bytes", t)
+
+
+def dte_type_set_plan(t: int, plan: int) -> None:
+    _ck(lib.dte_type_set_plan(t, plan), "dte_type_set_plan")
+
+
+def dte_type_get_plan(t: int) -> int:
+    v = C.c_int()
+    _ck(lib.dte_type_get_plan(t, C.byref(v)), "dte_type_get_plan")
+    return v.value
+
+
+def dte_op_shape_query(t: int, count: int, user: int, packed: int) -> dict:
+    """The shape of one operation as the kernels see it (dte_op_shape)."""
+    op = dte_op(t, count, user, packed)
+    out = dte_op_shape()
+    _ck(lib.dte_op_shape_query(C.byref(op), C.byref(out)), "dte_op_shape_query")
+    return {f: getattr(out, f) for f, _ in dte_op_shape._fields_}
 
 
 def dte_type_iov_len(t: int, max_iov_bytes: int):

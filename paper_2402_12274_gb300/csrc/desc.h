@@ -304,6 +304,16 @@ DTE_HD void decode_pos(const DNode *nodes, const char *blob, int node, int64_t P
     }
 }
 
+// Index list search of decode_seg: the entry of LIST node N that holds
+// segment k of one copy of N (the largest b with segment prefix <= k).
+DTE_HD int64_t list_entry_of_seg(const DNode *nodes, const char *blob, const DNode &N, int node, int64_t k,
+                                 Hint &h)
+{
+    if (N.flags & NF_PSEGS) return find_le(arr<int64_t>(blob, N.a_psegs), N.count, k, h, node);
+    const DNode &C0 = nodes[N.child];
+    return find_le(arr<int64_t>(blob, N.a_pbytes), N.count, fdiv(k, C0.div_nseg) * C0.size, h, node);
+}
+
 // ---------------------------------------------------------------------------
 // Merged segment index -> (displacement, length, packed offset where the
 // segment starts).  0 <= k < nseg.
@@ -351,12 +361,7 @@ DTE_HD void decode_seg(const DNode *nodes, const char *blob, int node, int64_t k
             len = (pb[b + 1] - pb[b]) + ext;
             return;
         }
-        if (N.flags & NF_PSEGS) {
-            b = find_le(arr<int64_t>(blob, N.a_psegs), N.count, k, h, node);
-        } else {
-            const DNode &C0 = nodes[N.child];
-            b = find_le(pb, N.count, fdiv(k, C0.div_nseg) * C0.size, h, node);
-        }
+        b = list_entry_of_seg(nodes, blob, N, node, k, h);
         int child;
         int64_t stride;
         uint8_t ef = N.a_eflags ? arr<uint8_t>(blob, N.a_eflags)[b] : 0;

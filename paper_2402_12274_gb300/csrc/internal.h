@@ -130,6 +130,7 @@ struct dte_type_s {
     int64_t size = 0, lb = 0, ub = 0, true_lb = 0, true_ub = 0;
     int64_t align = 1;             // natural alignment (max basic alignment)
     bool lb_x = false, ub_x = false, nonempty = false;
+    int plan = 0;                  // DTE_PLAN_* (dte_type_set_plan)
     dte::NP node;
     std::shared_ptr<dte::Committed> desc;
     int64_t extent() const { return ub - lb; }

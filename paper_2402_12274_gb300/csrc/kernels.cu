@@ -53,7 +53,7 @@ namespace dte {
 // order (see Spread), so costly and cheap regions of a layout are worked on
 // at the same time, while a span keeps consecutive steps together for the
 // search hints.
-template <int W, bool PACK, bool PK16>
+template <int W, bool PACK, bool PK16, bool WIDE = false>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) move_kernel(Desc d, Op op, int64_t nchunks, int64_t span,
                                                                    Spread sp)
 {
@@ -73,8 +73,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) move_kernel(Desc d, Op o
     for (int64_t j = warp; j < sp.nspans; j += nwarps) {
         const int64_t c0 = p * span;
         const int64_t c1 = min(c0 + span, nchunks);
-        for (int64_t base = c0; base < c1; base += kStepOf<W>)
-            warp_step<W, PACK, PK16>(op, nodes, blob, base, c1, lane, h, scr);
+        for (int64_t base = c0; base < c1; base += kStepOf<W, WIDE>)
+            warp_step<W, PACK, PK16, WIDE>(op, nodes, blob, base, c1, lane, h, scr);
         p += sp.inc;
         if (p >= sp.nspans) p -= sp.nspans;
     }
@@ -102,11 +102,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) seg_kernel(Desc d, Op op
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int64_t stride = (int64_t)gridDim.x * kWarps * span;
-    Hint h{-1, 0};
+    Hint h{-1, 0}, rh{-1, 0};
     for (int64_t s0 = warp * span; s0 < nsegs; s0 += stride) {
         const int64_t s1 = min(s0 + span, nsegs);
         for (int64_t base = s0; base < s1; base += 32)
-            seg_round<W, PACK>(op, nodes, blob, nseg_elem, div_nseg, seg0 + base, seg0 + s1, lane, h);
+            seg_round<W, PACK>(op, nodes, blob, nseg_elem, div_nseg, seg0 + base, seg0 + s1, lane, h, rh);
     }
 }
 
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) seg_kernel(Desc d, Op op
 // of `span` consecutive tiles in the spread order.  When the group's descriptors fit
 // in shared memory together (`image`, image_bytes > 0) they are staged once
 // per CTA and every op with soff >= 0 walks its staged copy.
-template <int W, bool PACK, bool PK16>
+template <int W, bool PACK, bool PK16, bool WIDE = false>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_kernel(const BatchOp *ops, const int64_t *tile0, int64_t nops,
                                                          int64_t ntiles, int64_t span, const char *image,
                                                          int64_t image_bytes, Spread sp)
@@ -158,8 +158,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_kernel(const Batch
             const int soff = b->soff;
             const char *blob = soff >= 0 ? reinterpret_cast<const char *>(smem) + soff : b->d.blob;
             const DNode *nodes = reinterpret_cast<const DNode *>(blob + sizeof(BlobHeader));
-            int64_t base = (t - tile0[i]) * kStepOf<W>;
-            warp_step<W, PACK, PK16>(wop[wid], nodes, blob, base, b->nchunks, lane, h, scr);
+            int64_t base = (t - tile0[i]) * kStepOf<W, WIDE>;
+            warp_step<W, PACK, PK16, WIDE>(wop[wid], nodes, blob, base, b->nchunks, lane, h, scr);
         }
     }
 }
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_seg_kernel(const B
     const int64_t warp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int64_t nwarps = (int64_t)gridDim.x * kWarps;
     Hint oh{-1, 0};
-    Hint h{-1, 0};
+    Hint h{-1, 0}, rh{-1, 0};
     int64_t cur = -1;
     int64_t p = spread_first(sp, warp);
     for (int64_t j = warp; j < sp.nspans; j += nwarps, p = p + sp.inc >= sp.nspans ? p + sp.inc - sp.nspans : p + sp.inc) {
@@ -198,6 +198,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_seg_kernel(const B
             const BatchOp *b = ops + i;
             if (i != cur) {
                 h = Hint{-1, 0};
+                rh = Hint{-1, 0};
                 cur = i;
                 load_op(wop[wid], b->op, lane);
             }
@@ -205,7 +206,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_seg_kernel(const B
             const char *blob = soff >= 0 ? reinterpret_cast<const char *>(smem) + soff : b->d.blob;
             const DNode *nodes = reinterpret_cast<const DNode *>(blob + sizeof(BlobHeader));
             const int64_t base = (t - tile0[i]) * 32;
-            seg_round<W, PACK>(wop[wid], nodes, blob, b->nseg_elem, b->div_nseg, base, b->nsegs, lane, h);
+            seg_round<W, PACK>(wop[wid], nodes, blob, b->nseg_elem, b->div_nseg, base, b->nsegs, lane, h, rh);
         }
     }
 }
@@ -221,6 +222,7 @@ static BatchKernel pick_batch(int wsel)
     case 10: return batch_seg_kernel<4, PACK>;
     case 11: return batch_seg_kernel<2, PACK>;
     case 12: return batch_seg_kernel<1, PACK>;
+    case kWideClass: return batch_kernel<16, PACK, true, true>;
     case 0: return batch_kernel<16, PACK, true>;
     case 1: return batch_kernel<8, PACK, true>;
     case 2: return batch_kernel<8, PACK, false>;
@@ -428,10 +430,10 @@ typedef void (*MoveKernel)(Desc, Op, int64_t, int64_t, Spread);
 
 
 template <bool PACK>
-static MoveKernel pick_move(int W, bool pk16)
+static MoveKernel pick_move(int W, bool pk16, bool wide)
 {
     switch (W) {
-    case 16: return move_kernel<16, PACK, true>;
+    case 16: return wide ? move_kernel<16, PACK, true, true> : move_kernel<16, PACK, true>;
     case 8: return pk16 ? move_kernel<8, PACK, true> : move_kernel<8, PACK, false>;
     case 4: return pk16 ? move_kernel<4, PACK, true> : move_kernel<4, PACK, false>;
     case 2: return pk16 ? move_kernel<2, PACK, true> : move_kernel<2, PACK, false>;
@@ -486,18 +488,20 @@ static int launch_move(bool pack, dte_type t, const char *dblob, const void *use
     if (op.total == 0) return DTE_SUCCESS;
     int W = word_of(c, t->extent(), count, user, packed);
     if (first != 0 || nbytes != count * c.size) W = (int)std::min<int64_t>(W, std::min(p2v(first), p2v(nbytes)));
+    const int plan = t->plan;
     bool pk16 = p2addr(packed) >= 16;
-    MoveKernel k = pack ? pick_move<true>(W, pk16) : pick_move<false>(W, pk16);
+    const bool wide = plan_wide(W, plan);
+    MoveKernel k = pack ? pick_move<true>(W, pk16, wide) : pick_move<false>(W, pk16, wide);
     size_t smem = 0;
     Desc d = make_desc(c, dblob, &smem);
     // occupancy per (device, direction, variant, staging mode); the staged
     // blob is sized for its upper bound
-    static thread_local int occ_cache[64][2][9][3];
-    int &occ = occ_cache[dev & 63][pack ? 1 : 0][wsel_of(W, pk16)][d.stage];
+    static thread_local int occ_cache[64][2][kNumClasses][3];
+    int &occ = occ_cache[dev & 63][pack ? 1 : 0][wide ? kWideClass : wsel_of(W, pk16)][d.stage];
     if (occ == 0) occ = occupancy(k, d.stage == STAGE_BLOB ? (size_t)kSmemBlob : smem);
     int64_t max_blocks = (int64_t)sm_count(dev) * occ;
     int64_t max_warps = max_blocks * kWarps;
-    if (use_seg_major(c, W)) {
+    if (plan_seg(c, W, plan)) {
         // short runs, small words: one decode per segment, cooperative copy
         typedef void (*SegKernel)(Desc, Op, int64_t, FastDiv, int64_t, int64_t, int64_t);
         SegKernel sk;
@@ -524,9 +528,11 @@ static int launch_move(bool pack, dte_type t, const char *dblob, const void *use
         }
         return DTE_SUCCESS;
     }
-    if (kBulk && W == 16 && nbytes >= kBulkMinTilesPerWarp * kBulkWarps * kBulkTile * sm_count(dev) &&
-        c.nseg > 0 && c.size / c.nseg >= kBulkMinRun &&
-        device_memory(user) && device_memory(packed)) {
+    const bool bulk_rule = plan == DTE_PLAN_BULK ||
+                           (plan == DTE_PLAN_AUTO && kBulk &&
+                            nbytes >= kBulkMinTilesPerWarp * kBulkWarps * kBulkTile * sm_count(dev) &&
+                            c.nseg > 0 && c.size / c.nseg >= kBulkMinRun);
+    if (bulk_rule && W == 16 && c.nseg > 0 && device_memory(user) && device_memory(packed)) {
         // long runs: bulk copies by the copy engine of each SM (bulk.cuh)
         allow_bulk_smem(dev);
         const int64_t buf_off = ((int64_t)smem + 127) & ~(int64_t)127;
@@ -542,7 +548,7 @@ static int launch_move(bool pack, dte_type t, const char *dblob, const void *use
         return DTE_SUCCESS;
     }
     int64_t nchunks = (op.total + 15) / 16;
-    const int64_t step = step_of_word(W);
+    const int64_t step = step_of_word(W, wide);
     int64_t steps = (nchunks + step - 1) / step;
     // span: one step when the descriptor sits in shared memory; up to eight
     // when index tables are searched in global memory (consecutive steps
@@ -854,7 +860,7 @@ int dte_batch_create(int kind, int64_t nops, const dte_op *ops, dte_batch *out)
                 if ((rc = device_blob(o.type, &dblob, &d2)) != DTE_SUCCESS) break;
                 Committed &c = *o.type->desc;
                 hc[(size_t)i] = &c;
-                fill_batch_op(h, c, o.type->extent(), o, dblob);
+                fill_batch_op(h, c, o.type->extent(), o, dblob, o.type->plan);
                 b->keep.push_back(o.type->desc);
             }
         }
@@ -1148,6 +1154,54 @@ int dte_type_iov_at_bytes_async(dte_type type, int64_t n, const int64_t *d_offse
     }
 }
 
+// The kernel class a single move and a batch op of `op` take (the same
+// decisions as launch_move and fill_batch_op).
+int dte_op_shape_query(const dte_op *op, dte_op_shape *out)
+{
+    try {
+        if (!op || !out) return DTE_ERR_ARG;
+        if (!handle_valid(op->type)) return DTE_ERR_TYPE;
+        if (!op->type->committed) return DTE_ERR_TYPE;
+        if (op->count < 0) return DTE_ERR_ARG;
+        const Committed &c = *op->type->desc;
+        const int64_t ext = op->type->extent();
+        int64_t bytes, segs;
+        if (__builtin_mul_overflow(op->count, c.size, &bytes) || __builtin_mul_overflow(op->count, c.nseg, &segs))
+            return DTE_ERR_OVERFLOW;
+        const int plan = op->type->plan;
+        const int W = word_of(c, ext, op->count, op->user, op->packed);
+        dte_op_shape r;
+        r.word = W;
+        r.list = c.big_list ? 1 : 0;
+        r.bytes = bytes;
+        r.segments = segs;
+        r.max_run = c.maxrun;
+        const int batch = plan_seg(c, W, plan) ? DTE_PLAN_SEGMENT : plan_wide(W, plan) ? DTE_PLAN_CHUNK_WIDE
+                                                                                        : DTE_PLAN_CHUNK;
+        r.batch_kernel = batch;
+        r.single_kernel = batch;
+        if (batch != DTE_PLAN_SEGMENT && W == 16 && c.nseg > 0) {
+            int dev = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess) {
+                cudaGetLastError();
+                dev = -1;
+            }
+            const bool rule = plan == DTE_PLAN_BULK ||
+                              (plan == DTE_PLAN_AUTO && kBulk && dev >= 0 &&
+                               bytes >= kBulkMinTilesPerWarp * kBulkWarps * kBulkTile * sm_count(dev) &&
+                               c.size / c.nseg >= kBulkMinRun);
+            if (rule && dev >= 0 && device_memory(op->user) && device_memory(op->packed))
+                r.single_kernel = DTE_PLAN_BULK;
+        }
+        *out = r;
+        return DTE_SUCCESS;
+    } catch (const Error &e) {
+        return e.code;
+    } catch (...) {
+        return DTE_ERR_NOMEM;
+    }
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
@@ -1233,7 +1287,7 @@ extern "C" int dte_pack_batch_enqueue_noalloc(int64_t nops, const dte_op *ops, d
             const char *dblob;
             // the descriptor must already be on this device (commit uploads it)
             if (int rc = device_blob_resident(o.type, dev, &dblob)) return rc;
-            fill_batch_op(h, *o.type->desc, o.type->extent(), o, dblob);
+            fill_batch_op(h, *o.type->desc, o.type->extent(), o, dblob, o.type->plan);
         }
         // group by kernel variant exactly like the allocating batch
         struct G { int wsel; int64_t op0, nops, t0, ntiles; };

@@ -30,11 +30,16 @@ constexpr int kStep = 32 * kU;        // chunks per warp step (2 KiB)
 #ifndef DTE_KU16
 #define DTE_KU16 2
 #endif
-template <int W>
-constexpr int kUOf = W == 16 ? DTE_KU16 : kU;
-template <int W>
-constexpr int kStepOf = 32 * kUOf<W>;
-static inline int64_t step_of_word(int W) { return W == 16 ? kStepOf<16> : kStep; }
+// The wide plan (DTE_PLAN_CHUNK_WIDE) gives 16-byte moves 2 KiB steps (four
+// chunks per lane) instead.
+template <int W, bool WIDE = false>
+constexpr int kUOf = W == 16 ? (WIDE ? 4 : DTE_KU16) : kU;
+template <int W, bool WIDE = false>
+constexpr int kStepOf = 32 * kUOf<W, WIDE>;
+static inline int64_t step_of_word(int W, bool wide = false)
+{
+    return W == 16 ? (wide ? kStepOf<16, true> : kStepOf<16>) : kStep;
+}
 #ifndef DTE_MINBLOCKS
 #define DTE_MINBLOCKS 4
 #endif
@@ -55,6 +60,19 @@ static bool use_seg_major(const Committed &c, int W)
 {
     return W < 16 && c.big_list && c.maxrun <= kSegMaxRun && c.nseg > 0 && c.size / c.nseg <= kSegMaxMean;
 }
+
+// Kernel class of a move under a type's plan (include/dte.h, dte_plan): the
+// fixed rule above for DTE_PLAN_AUTO; otherwise the plan where it applies --
+// segment-major needs a copy word below 16 bytes and runs of at most
+// kSegMaxRun, the wide step a 16-byte word -- and the fixed rule's choice
+// where it does not.
+static bool plan_seg(const Committed &c, int W, int plan)
+{
+    if (plan == DTE_PLAN_CHUNK) return false;
+    if (plan == DTE_PLAN_SEGMENT && W < 16 && c.nseg > 0 && c.maxrun <= kSegMaxRun) return true;
+    return use_seg_major(c, W);  // the fixed rule: AUTO, and plans that do not apply
+}
+static bool plan_wide(int W, int plan) { return W == 16 && plan == DTE_PLAN_CHUNK_WIDE; }
 constexpr int kMaxSmemNodes = 64;
 
 enum : int { STAGE_NONE = 0, STAGE_NODES = 1, STAGE_BLOB = 2 };
@@ -291,27 +309,28 @@ __device__ __forceinline__ void store_packed(char *p, uint4 v, int nb)
 template <int W>
 constexpr int kScratch = W < 16 ? kThreads : 1;
 
-// One warp step, 16-byte words: a lane's chunks sit 512 bytes apart, so when
-// the run found for its first chunk extends past a later chunk, that chunk's
-// user address follows without walking the descriptor again.
-template <bool PACK>
+// One warp step, 16-byte words, U chunks per lane: a lane's chunks sit 512
+// bytes apart, so when the run found for its first chunk extends past a later
+// chunk, that chunk's user address follows without walking the descriptor
+// again.
+template <bool PACK, int U>
 __device__ __forceinline__ void warp_step16(const Op &op, const DNode *nodes, const char *blob, int64_t base,
                                             int64_t end, int lane, Hint &h)
 {
-    uint4 v[kUOf<16>];
-    int64_t d[kUOf<16>];
+    uint4 v[U];
+    int64_t d[U];
     int64_t d0 = 0, rem0 = 0;
     if (!PACK) {
         // the packed side is addressed by position alone: its loads go out
         // before the descriptor walks, whose latency they then cover
 #pragma unroll
-        for (int u = 0; u < kUOf<16>; u++) {
+        for (int u = 0; u < U; u++) {
             int64_t c = base + u * 32 + lane;
             if (c < end) v[u] = __ldg(reinterpret_cast<const uint4 *>(op.packed_in + c * 16));
         }
     }
 #pragma unroll
-    for (int u = 0; u < kUOf<16>; u++) {
+    for (int u = 0; u < U; u++) {
         int64_t c = base + u * 32 + lane;
         if (c < end) {
             if (u > 0 && rem0 >= (int64_t)u * 512 + 16) {
@@ -328,7 +347,7 @@ __device__ __forceinline__ void warp_step16(const Op &op, const DNode *nodes, co
         }
     }
 #pragma unroll
-    for (int u = 0; u < kUOf<16>; u++) {
+    for (int u = 0; u < U; u++) {
         int64_t c = base + u * 32 + lane;
         if (c < end) {
             if (PACK) *reinterpret_cast<uint4 *>(op.packed_out + c * 16) = v[u];
@@ -337,13 +356,13 @@ __device__ __forceinline__ void warp_step16(const Op &op, const DNode *nodes, co
     }
 }
 
-// One warp step: chunks [base, base + kStepOf<W>) clipped to `end`.
-template <int W, bool PACK, bool PK16>
+// One warp step: chunks [base, base + kStepOf<W, WIDE>) clipped to `end`.
+template <int W, bool PACK, bool PK16, bool WIDE = false>
 __device__ __forceinline__ void warp_step(const Op &op, const DNode *nodes, const char *blob, int64_t base,
                                           int64_t end, int lane, Hint &h, char *scr)
 {
     if constexpr (W == 16) {
-        warp_step16<PACK>(op, nodes, blob, base, end, lane, h);
+        warp_step16<PACK, kUOf<16, WIDE>>(op, nodes, blob, base, end, lane, h);
     } else {
         uint4 v[kU];
 #pragma unroll
@@ -372,16 +391,74 @@ __device__ __forceinline__ void warp_step(const Op &op, const DNode *nodes, cons
 // ---------------------------------------------------------------------------
 // segment-major round
 // ---------------------------------------------------------------------------
+// Whether a round can be decoded by shared_list_round: the element's root is
+// a large index list whose entries all repeat one child at one stride (an
+// indexed or hindexed type of any old type) with no segment merging across
+// or inside entries, so entry b starts at segment (pbytes[b] / child size) *
+// child segments and every entry has at least one segment.
+__device__ __forceinline__ bool shared_list_root(const DNode &R)
+{
+    return R.kind == NK_LIST && (R.flags & NF_SHARED) &&
+           !(R.flags & (NF_RUNS | NF_PSEGS | NF_XMERGE | NF_EMERGE)) && R.a_eflags == 0 && R.count > 32;
+}
+
+// Decode of a round's segments local0 .. local0 + nvalid - 1 (all of element
+// e0) under such a root, by the warp together.  Those segments lie in at most
+// 32 consecutive entries starting with b0, the entry of the first one (one
+// warp-uniform search from the warp's hint rh, which each round leaves at the
+// entry of its last segment).  Lane j loads entry b0 + j's packed prefix and
+// displacement (coalesced) and computes its first segment; one OR-reduction
+// marks where entries start inside the round, so lane l's entry is b0 plus the
+// number of entries starting in (local0, local0 + l], and lane l takes that
+// entry's values by shuffle.  Only the child (the entry's repeated type) is
+// walked per lane.  Same results as decode_seg on the root.
+__device__ __forceinline__ void shared_list_round(const Op &op, const DNode *nodes, const char *blob, const DNode &R,
+                                                  int64_t e0, int64_t local0, int nvalid, int lane, Hint &rh,
+                                                  Hint &h, int64_t &disp, int64_t &len, int64_t &ps)
+{
+    const unsigned FULL = 0xffffffffu;
+    const DNode &C = nodes[R.child];
+    const int64_t *pb = arr<int64_t>(blob, R.a_pbytes);
+    const int64_t *dv = arr<int64_t>(blob, R.a_disp);
+    const int64_t b0 = find_le(pb, R.count, fdiv(local0, C.div_nseg) * C.size, rh, op.root);
+    const int64_t bj = b0 + lane;
+    const int64_t pbj = bj <= R.count ? pb[bj] : INT64_MAX;
+    const int64_t dj = bj < R.count ? dv[bj] : 0;
+    const int64_t sj = bj <= R.count ? fdiv(pbj, C.div_size) * C.nseg : INT64_MAX;
+    const int64_t o = sj - local0;
+    const unsigned starts = __reduce_or_sync(FULL, (lane > 0 && o > 0 && o < 32) ? 1u << (int)o : 0u);
+    const int jl = __popc(starts & (0xffffffffu >> (31 - lane)));
+    const int64_t pbe = __shfl_sync(FULL, pbj, jl);
+    const int64_t de = __shfl_sync(FULL, dj, jl);
+    const int64_t se = __shfl_sync(FULL, sj, jl);
+    rh.b = b0 + __shfl_sync(FULL, jl, nvalid - 1);
+    if (lane < nvalid) {
+        const int64_t local = local0 + lane - se;
+        const int64_t i = fdiv(local, C.div_nseg);
+        disp = e0 * op.extent + R.base + de + i * R.stride;
+        int64_t pc;
+        decode_seg(nodes, blob, R.child, local - i * C.nseg, disp, len, pc, h);
+        ps = e0 * op.esize + pbe + i * C.size + pc;
+    }
+}
+
 // One round: segments [base, base + 32) clipped to s1 (warp-uniform args).
+// `rh` is the warp's search position in a root index list.
 template <int W, bool PACK>
 __device__ __forceinline__ void seg_round(const Op &op, const DNode *nodes, const char *blob, int64_t nseg_elem,
-                                          const FastDiv &div_nseg, int64_t base, int64_t s1, int lane, Hint &h)
+                                          const FastDiv &div_nseg, int64_t base, int64_t s1, int lane, Hint &h,
+                                          Hint &rh)
 {
     using T = typename Word<W>::T;
     const unsigned FULL = 0xffffffffu;
     const int nvalid = (int)min((int64_t)32, s1 - base);
     int64_t disp = 0, len = 0, ps = 0;
-    if (lane < nvalid) {
+    const DNode &R = nodes[op.root];
+    const int64_t e0 = fdiv(base, div_nseg);
+    const int64_t local0 = base - e0 * nseg_elem;
+    if (shared_list_root(R) && local0 + nvalid <= nseg_elem) {
+        shared_list_round(op, nodes, blob, R, e0, local0, nvalid, lane, rh, h, disp, len, ps);
+    } else if (lane < nvalid) {
         const int64_t k = base + lane;
         const int64_t e = fdiv(k, div_nseg);
         disp = e * op.extent;
@@ -451,7 +528,8 @@ struct BatchOp {
     FastDiv div_nseg;
 };
 
-constexpr int kNumClasses = 13;  // 9 chunk-major word classes + 4 segment-major
+constexpr int kNumClasses = 14;  // 9 chunk-major word classes + 4 segment-major + wide 16-byte steps
+constexpr int kWideClass = 13;
 
 __host__ __device__ constexpr int wsel_of(int W, bool pk16)
 {
@@ -591,8 +669,10 @@ static int prep(dte_type t, dte_stream_t stream, const char **blob, int *dev)
 }
 
 // Fill one op record: copy word, kernel variant (segment-major by the same
-// rule as single ops) and its work size.
-static void fill_batch_op(BatchOp &h, const Committed &c, int64_t extent, const dte_op &o, const char *dblob)
+// rule as single ops, under the type's plan) and its work size.  A batch has
+// no bulk-copy variant: DTE_PLAN_BULK takes the fixed rule there.
+static void fill_batch_op(BatchOp &h, const Committed &c, int64_t extent, const dte_op &o, const char *dblob,
+                          int plan)
 {
     size_t smem;
     h.d = make_desc(c, dblob, &smem);
@@ -600,22 +680,24 @@ static void fill_batch_op(BatchOp &h, const Committed &c, int64_t extent, const 
     h.op = make_op(c, extent, o.user, o.packed, o.count);
     h.nchunks = (h.op.total + 15) / 16;
     int W = word_of(c, extent, o.count, o.user, o.packed);
-    if (use_seg_major(c, W)) {
+    if (plan_seg(c, W, plan)) {
         h.wsel = seg_class(W);
         h.nseg_elem = c.nseg;
         h.nsegs = o.count * c.nseg;
         h.div_nseg = c.nodes()[c.root].div_nseg;
+    } else if (plan_wide(W, plan)) {
+        h.wsel = kWideClass;
     } else {
         h.wsel = wsel_of(W, p2addr(o.packed) >= 16);
     }
 }
 
-// tiles of an op: warp steps (1 KiB for 16-byte words, 2 KiB otherwise) or
-// rounds of 32 segments
+// tiles of an op: warp steps (1 KiB for 16-byte words, 2 KiB for the wide
+// class and the sub-16-byte words) or rounds of 32 segments
 static int64_t op_tiles(const BatchOp &h)
 {
-    if (h.wsel >= 9) return (h.nsegs + 31) / 32;
-    const int64_t st = h.wsel == 0 ? kStepOf<16> : kStep;  // class 0 is the 16-byte word
+    if (h.wsel >= 9 && h.wsel < kWideClass) return (h.nsegs + 31) / 32;
+    const int64_t st = h.wsel == 0 ? kStepOf<16> : h.wsel == kWideClass ? kStepOf<16, true> : kStep;
     return (h.nchunks + st - 1) / st;
 }
 

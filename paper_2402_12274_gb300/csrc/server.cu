@@ -10,18 +10,21 @@
 //
 //   host                                   device (persistent kernel)
 //   ----                                   ---------------------------
-//   submit -> FIFO; admit while ring       warps walk the published requests
-//   slots and the byte cap allow: write    in order and claim tiles with a
-//   the record, then publish (release)     fetch-add on the slot's counter,
-//                                          tagged with the request number so a
-//                                          reused slot is never confused; the
-//                                          record is mirrored into device memory
-//   progress: read completion words        the last warp of a request writes its
-//   (acquire), free capacity, admit more   completion word (release, system scope)
+//   submit -> FIFO; admit while ring       one warp mirrors newly published
+//   slots and the byte cap allow: write    requests into device memory and
+//   the record, then publish (release)     appends their tiles to one global
+//                                          tile sequence; the other warps
+//                                          claim ranges of it with one
+//                                          fetch-add on a single counter,
+//                                          sized by the tiles still unclaimed
+//   progress: read completion words        the warp that finishes a request's
+//   (acquire), free capacity, admit more   last tile writes its completion word
 //
 // Every device wait is bounded: a warp that finds nothing to do polls with
-// __nanosleep and leaves after `idle_limit` empty polls; the host relaunches
-// the loop when work arrives after it left.  A host stop flag ends it at once.
+// __nanosleep and leaves after `idle_limit` of empty polls (a claim it still
+// holds is kept in device memory for the same warp of the next launch); the
+// host relaunches the loop when work arrives after it left.  A host stop flag
+// ends it at once.
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -73,13 +76,13 @@ __device__ __forceinline__ void st_release_sys(int64_t *p, int64_t v)
 // each variant for the whole loop, one call per claim).  The search hint h
 // is the warp's, kept while it works on the same request, so consecutive
 // tiles of a large index table continue the search where it stopped.
-template <int W, bool PACK, bool PK16>
+template <int W, bool PACK, bool PK16, bool WIDE = false>
 __device__ __noinline__ void serve_chunk_span(const BatchOp *b, int64_t t, int64_t k, int lane, char *scr, Hint &h)
 {
     const char *blob = b->d.blob;
     const DNode *nodes = reinterpret_cast<const DNode *>(blob + sizeof(BlobHeader));
     for (int64_t tt = t; tt < t + k; tt++)
-        warp_step<W, PACK, PK16>(b->op, nodes, blob, tt * kStepOf<W>, b->nchunks, lane, h, scr);
+        warp_step<W, PACK, PK16, WIDE>(b->op, nodes, blob, tt * kStepOf<W, WIDE>, b->nchunks, lane, h, scr);
 }
 
 template <int W, bool PACK>
@@ -87,14 +90,16 @@ __device__ __noinline__ void serve_seg_span(const BatchOp *b, int64_t t, int64_t
 {
     const char *blob = b->d.blob;
     const DNode *nodes = reinterpret_cast<const DNode *>(blob + sizeof(BlobHeader));
+    Hint rh{-1, 0};
     for (int64_t tt = t; tt < t + k; tt++)
-        seg_round<W, PACK>(b->op, nodes, blob, b->nseg_elem, b->div_nseg, tt * 32, b->nsegs, lane, h);
+        seg_round<W, PACK>(b->op, nodes, blob, b->nseg_elem, b->div_nseg, tt * 32, b->nsegs, lane, h, rh);
 }
 
 template <bool PACK>
 __device__ __forceinline__ void serve_span_dir(const BatchOp *b, int64_t t, int64_t k, int lane, char *scr, Hint &h)
 {
     switch (b->wsel) {
+    case kWideClass: serve_chunk_span<16, PACK, true, true>(b, t, k, lane, scr, h); break;
     case 0: serve_chunk_span<16, PACK, true>(b, t, k, lane, scr, h); break;
     case 1: serve_chunk_span<8, PACK, true>(b, t, k, lane, scr, h); break;
     case 2: serve_chunk_span<8, PACK, false>(b, t, k, lane, scr, h); break;
@@ -111,15 +116,6 @@ __device__ __forceinline__ void serve_span_dir(const BatchOp *b, int64_t t, int6
     }
 }
 
-// Device state of the loop (device memory, zero at creation); the per-slot
-// tile counters, completion counters and mirrored records follow it.
-struct DevState {
-    unsigned long long cur;   // oldest request still being handed out
-    unsigned long long dpub;  // requests mirrored into device memory
-    int mlock;                // try-lock of the warp mirroring new requests
-    int pad_;
-};
-
 __device__ __forceinline__ unsigned long long ld_relaxed_gpu(const unsigned long long *p)
 {
     unsigned long long v;
@@ -134,136 +130,299 @@ __device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long
     return v;
 }
 
-// Warps claim tiles with fetch-adds on the slot counter of the oldest request
-// being handed out; a counter holds (request << 36 | next tile), so a warp
-// whose view of the oldest request is stale still learns from the counter
-// which request its tiles belong to.  Counters are re-tagged only when a
-// request is mirrored into its slot, which the host allows only after the
-// slot's previous request completed, so no claimed tile is ever lost.  The
-// host side of the ring (pinned memory) is touched only by the warp that
-// mirrors new requests and by idle warps.
+// Device state of the loop (device memory, zero at creation).  The claim
+// counter sits alone on its own 128-byte line: every claim is a fetch-add on
+// it, while the words the mirroring warp publishes are read by every warp.
+struct alignas(128) ClaimLine {
+    unsigned long long next;   // next unclaimed tile of the global sequence
+};
+struct alignas(128) PubLine {
+    unsigned long long total;  // tiles of all mirrored requests (the sequence's length)
+    unsigned long long dpub;   // requests mirrored into device memory
+    int mirror_gone;           // the mirroring warp has left (reset before each launch)
+};
+struct SlotTile {              // where a mirrored request's tiles start
+    long long tag;             // the request number (slots are reused)
+    long long first;           // its first tile in the global sequence
+};
+struct Held {                  // a warp's claim, kept across launches of the loop
+    long long next, end;
+};
+
+struct ServeArgs {
+    const SlotRec *ring;       // pinned host ring of admitted requests
+    Ctrl *ctrl;                // pinned host control words
+    int64_t *comp;             // pinned completion words, one per slot
+    ClaimLine *claim;
+    PubLine *pub;
+    SlotTile *stile;           // per slot
+    unsigned long long *done;  // per slot: tiles finished
+    SlotRec *dring;            // per slot: mirrored record
+    Held *held;                // per warp of the grid
+    int64_t mask, slots;
+    int64_t span_min, span_max;
+    int64_t idle_budget_ns;
+};
+
+// Which mirrored request holds global tile c (c < total, read after the
+// acquire of total), searched by the whole warp.  Requests [dpub - slots,
+// dpub) sit in their slots unless they completed and the host reused the
+// slot; a reused slot belongs to a request older than c's (the host admits in
+// order and reuses a slot only after its request completed, and c's request
+// has not), so a slot whose tag is not its request number counts as "starts
+// at or before c".  The predicate "starts at or before c" is then true for
+// every request up to c's and false after it.  `lo` satisfies it.  Each pass
+// probes 32 evenly spaced requests of [lo, hi) at once and keeps the stretch
+// after the last one that satisfies it: two passes for a ring of 1024 slots.
+// Requests without tiles share their successor's first tile and are passed
+// over.  Returns -1 if lo itself fails (never expected: the caller retries).
+__device__ __forceinline__ long long request_of_tile(const ServeArgs &a, long long lo, long long hi, long long c,
+                                                     int lane)
+{
+    const unsigned FULL = 0xffffffffu;
+    while (hi - lo > 1) {
+        const long long step = (hi - lo + 31) >> 5;
+        const long long p = lo + (long long)lane * step;
+        bool starts_before = false;
+        if (p < hi) {
+            const SlotTile *st = a.stile + (p & a.mask);
+            // first is published with a release after tag: acquiring it orders
+            // the tag read after it, so a tag that still matches goes with its
+            // own first
+            long long f, tg;
+            asm volatile("ld.acquire.gpu.global.s64 %0, [%1];" : "=l"(f) : "l"(&st->first) : "memory");
+            asm volatile("ld.relaxed.gpu.global.s64 %0, [%1];" : "=l"(tg) : "l"(&st->tag) : "memory");
+            starts_before = tg != p || f <= c;
+        }
+        const unsigned m = __ballot_sync(FULL, starts_before);
+        if (m == 0) return -1;
+        const long long j = 31 - __clz(m);
+        lo += j * step;
+        hi = min(lo + step, hi);
+    }
+    return lo;
+}
+
 #ifndef DTE_SERVE_CTAS
 #define DTE_SERVE_CTAS 2
 #endif
 constexpr int kServeCtas = DTE_SERVE_CTAS;  // most CTAs per SM the loop is compiled for
 
-__global__ void __launch_bounds__(kThreads, kServeCtas)
-    serve_kernel(const SlotRec *ring, int64_t mask, Ctrl *ctrl, DevState *st, unsigned long long *ctr,
-                 unsigned long long *done, SlotRec *dring, int64_t *comp, int64_t span, int64_t idle_budget_ns)
+// The mirroring warp (warp 0 of CTA 0) does nothing else: it polls the host's
+// publication count, copies new records from pinned host memory into device
+// memory, gives each request its range of the global tile sequence, and then
+// publishes the new total.  Every other warp claims ranges [next, next + k)
+// of that sequence with one fetch-add (which always succeeds: a
+// compare-and-swap claim fails whenever another claim lands between reading
+// the counter and swapping it, which at this claim rate is nearly always).  k
+// shrinks with the published tiles left unclaimed (guided self-scheduling:
+// about half of them spread over all warps, at most span_max, at least
+// span_min while many are left and 1 near the end), so a large request is
+// handed out in a few large claims and the last tiles of a burst one by one.
+// A claim may cover the ends of several requests, which are processed in
+// turn, and may run past the published total when warps race for the last
+// tiles (an over-claim, at most k tiles per warp): the warp keeps those tiles
+// and processes them once the requests they belong to are published.  Tiles
+// are never handed out twice (fetch-adds give disjoint ranges) and never
+// dropped: a warp gives up a range only by finishing it, and a warp that
+// leaves while holding one stores it in held[] for the same warp of the next
+// launch (the grid size is fixed per loop).
+__global__ void __launch_bounds__(kThreads, kServeCtas) serve_kernel(ServeArgs a)
 {
     __shared__ BatchOp wop[kWarps];
     __shared__ uint4 scratch[kThreads];  // chunk assembly for the sub-16-byte word classes
     char *scr = reinterpret_cast<char *>(&scratch[threadIdx.x]);
     __shared__ int32_t wkind[kWarps];
-    __shared__ int64_t wntiles[kWarps];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
-    int64_t cached = -1;
-    Hint h{-1, 0};  // search position in the current request's descriptor
+    const bool mirror = blockIdx.x == 0 && w == 0;
+    const long long nwarps = (long long)gridDim.x * kWarps - 1;  // claiming warps
     int64_t idle_ns = 0;
-    unsigned backoff = 256;
-    for (;;) {
-        int action = 0;  // 0 idle, 1 work, 2 leave, 3 retry, 4 mirror
-        int64_t r = 0, t = 0, k = 0;
-        if (lane == 0) {
-            const unsigned long long c = ld_relaxed_gpu(&st->cur);
-            const unsigned long long pub = ld_acquire_gpu(&st->dpub);
-            if (c >= pub) {
-                const int64_t P = ld_acquire_sys(&ctrl->published);
-                if ((unsigned long long)P > pub) {
-                    action = atomicCAS(&st->mlock, 0, 1) == 0 ? 4 : 3;
-                    r = P;
-                } else {
-                    action = ld_relaxed_sys(&ctrl->stop) ? 2 : 0;
-                }
-            } else {
-                const int64_t slot = (int64_t)(c & (unsigned long long)mask);
-                const unsigned long long v = atomicAdd(ctr + slot, (unsigned long long)span);
-                __threadfence();
-                const int64_t tag = (int64_t)(v >> kTagBits);
-                t = (int64_t)(v & kTileMask);
-                const int64_t nt = (int64_t)ld_relaxed_gpu(reinterpret_cast<const unsigned long long *>(&dring[slot].ntiles));
-                if (t >= nt) {
-                    atomicMax(&st->cur, (unsigned long long)(tag + 1));
-                    if (t == 0 && nt == 0) {  // empty request: its first claimer completes it
-                        __threadfence_system();
-                        st_release_sys(comp + slot, tag + 1);
-                    }
-                    action = 3;
-                } else {
-                    r = tag;
-                    k = min(span, nt - t);
-                    action = 1;
-                    wntiles[w] = nt;
-                }
+    unsigned backoff = 128;
+    if (mirror) {
+        // this warp is the only writer of dpub and total: it reads them once
+        // (past L1) and keeps them in registers; a plain load could return a
+        // stale L1 copy of a word that the atomics below update in L2
+        long long from = (long long)ld_relaxed_gpu(&a.pub->dpub);
+        long long tt = (long long)ld_relaxed_gpu(&a.pub->total);
+        for (;;) {
+            long long P = 0;
+            bool stop = false;
+            if (lane == 0) {
+                P = ld_acquire_sys(&a.ctrl->published);
+                stop = ld_relaxed_sys(&a.ctrl->stop) != 0;
             }
-        }
-        action = __shfl_sync(FULL, action, 0);
-        if (action == 2) break;
-        if (action == 3) continue;
-        if (action == 0) {
-            idle_ns += backoff;
-            if (idle_ns > idle_budget_ns) break;  // bounded: the host relaunches when work arrives
-            __nanosleep(backoff);
-            backoff = backoff < 8192 ? backoff * 2 : 8192;
-            continue;
-        }
-        idle_ns = 0;
-        backoff = 256;
-        r = __shfl_sync(FULL, r, 0);
-        if (action == 4) {
-            // mirror requests [dpub, P) from pinned host memory into device memory
-            const int64_t from = (int64_t)ld_relaxed_gpu(&st->dpub);
-            ld_acquire_sys(&ctrl->published);  // each lane orders its reads after the publication
-            for (int64_t q = from; q < r; q++) {
-                const int64_t *src = reinterpret_cast<const int64_t *>(ring + (q & mask));
-                int64_t *dst = reinterpret_cast<int64_t *>(dring + (q & mask));
+            P = __shfl_sync(FULL, P, 0);
+            if (__shfl_sync(FULL, (int)stop, 0)) break;
+            if (P <= from) {
+                idle_ns += backoff;
+                if (idle_ns > a.idle_budget_ns) {
+                    // bounded: the host relaunches the loop on demand; the
+                    // other warps leave once they run out of tiles
+                    if (lane == 0) atomicExch(&a.pub->mirror_gone, 1);
+                    break;
+                }
+                __nanosleep(backoff);
+                backoff = backoff < 2048 ? backoff * 2 : 2048;
+                continue;
+            }
+            idle_ns = 0;
+            backoff = 128;
+            ld_acquire_sys(&a.ctrl->published);  // each lane orders its reads after the publication
+            for (long long qq = from; qq < P; qq++) {
+                const int64_t *src = reinterpret_cast<const int64_t *>(a.ring + (qq & a.mask));
+                int64_t *dst = reinterpret_cast<int64_t *>(a.dring + (qq & a.mask));
                 for (int i = lane; i < (int)(sizeof(SlotRec) / 8); i += 32) dst[i] = ld_relaxed_sys(src + i);
             }
             __threadfence();
             __syncwarp();
             if (lane == 0) {
-                for (int64_t q = from; q < r; q++) ctr[q & mask] = ((unsigned long long)q) << kTagBits;
+                for (long long qq = from; qq < P; qq++) {
+                    const long long slot = qq & a.mask;
+                    const long long nt = (long long)ld_relaxed_gpu(
+                        reinterpret_cast<const unsigned long long *>(&a.dring[slot].ntiles));
+                    a.done[slot] = 0;
+                    a.stile[slot].tag = qq;
+                    asm volatile("st.release.gpu.global.s64 [%0], %1;" ::"l"(&a.stile[slot].first), "l"(tt)
+                                 : "memory");
+                    if (nt == 0) {  // nothing to move: complete at once
+                        __threadfence_system();
+                        st_release_sys(a.comp + slot, qq + 1);
+                    }
+                    tt += nt;
+                }
                 __threadfence();
-                atomicExch(&st->dpub, (unsigned long long)r);
+                // dpub before total: a warp that acquires the new total finds
+                // every request its tiles belong to
+                atomicExch(&a.pub->dpub, (unsigned long long)P);
                 __threadfence();
-                atomicExch(&st->mlock, 0);
+                atomicExch(&a.pub->total, (unsigned long long)tt);
             }
+            tt = __shfl_sync(FULL, tt, 0);
+            from = P;
             __syncwarp();
+        }
+        return;
+    }
+    // lane 0's claim [cn, ce) and the request last found
+    const int64_t gw = (int64_t)blockIdx.x * kWarps + w;
+    long long cn = 0, ce = 0, q = -1, qfirst = 0, qnt = 0;
+    if (lane == 0) {
+        cn = a.held[gw].next;
+        ce = a.held[gw].end;
+        a.held[gw] = Held{0, 0};
+    }
+    int64_t cached = -1;  // request whose record is in wop[w]
+    Hint h{-1, 0};        // search position in that request's descriptor
+    for (;;) {
+        int have = 0;
+        if (lane == 0) {
+            const long long TT = (long long)ld_acquire_gpu(&a.pub->total);
+            if (cn >= ce) {
+                const long long G = (long long)ld_relaxed_gpu(&a.claim->next);
+                if (G < TT) {
+                    long long k = (TT - G) / (2 * nwarps);
+                    const long long lo = TT - G >= a.span_min * nwarps ? a.span_min : 1;
+                    k = k < lo ? lo : k > a.span_max ? a.span_max : k;
+                    cn = (long long)atomicAdd(&a.claim->next, (unsigned long long)k);
+                    ce = cn + k;
+                }
+            }
+            have = cn < ce && cn < TT;
+        }
+        if (!__shfl_sync(FULL, have, 0)) {
+            // nothing published to work on: wait (an over-claim waits for its
+            // tiles); leave on stop, when the mirroring warp has left (nothing
+            // more is published in this launch), or after the idle budget --
+            // keeping any claim for the same warp of the next launch
+            if (lane == 0) {
+                int gone;
+                asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(gone) : "l"(&a.pub->mirror_gone) : "memory");
+                have = gone || ld_relaxed_sys(&a.ctrl->stop) != 0;
+            }
+            idle_ns += backoff;
+            if (__shfl_sync(FULL, have, 0) || idle_ns > a.idle_budget_ns) {
+                if (lane == 0 && cn < ce) a.held[gw] = Held{cn, ce};
+                break;
+            }
+            __nanosleep(backoff);
+            const unsigned cap = __shfl_sync(FULL, (int)(cn < ce), 0) ? 512u : 2048u;
+            backoff = backoff < cap ? backoff * 2 : cap;
             continue;
         }
-        t = __shfl_sync(FULL, t, 0);
-        k = __shfl_sync(FULL, k, 0);
-        __syncwarp();  // lane 0's fence after the counter orders the other lanes' reads below
+        backoff = 128;
+        // the request holding tile cn (lane 0's cached one, else a warp search)
+        long long c = __shfl_sync(FULL, cn, 0);
+        if (__shfl_sync(FULL, (int)(q < 0 || c < qfirst || c >= qfirst + qnt), 0)) {
+            // the total acquired before the claim bounds c; dpub was stored
+            // before that total, so every request holding tiles below it is
+            // among [.., dpub)
+            long long dp = 0;
+            if (lane == 0) dp = (long long)ld_relaxed_gpu(&a.pub->dpub);
+            dp = __shfl_sync(FULL, dp, 0);
+            long long lo = dp - a.slots > 0 ? dp - a.slots : 0;
+            const long long qh = __shfl_sync(FULL, q, 0);
+            if (qh > lo && qh < dp) lo = qh;  // claims only move forward
+            const long long found = request_of_tile(a, lo, dp, c, lane);
+            if (lane == 0) {
+                q = found;
+                if (q >= 0) {
+                    qfirst = (long long)ld_relaxed_gpu(
+                        reinterpret_cast<const unsigned long long *>(&a.stile[q & a.mask].first));
+                    qnt = (long long)ld_relaxed_gpu(
+                        reinterpret_cast<const unsigned long long *>(&a.dring[q & a.mask].ntiles));
+                    if (c < qfirst || c >= qfirst + qnt) q = -1;  // never expected: search again
+                }
+            }
+            if (__shfl_sync(FULL, (int)(q < 0), 0)) {
+                // bounded like an idle poll; a loop that gives up leaves the
+                // claim's request incomplete, which the host's bounded wait
+                // reports as a timeout
+                idle_ns += 256;
+                if (idle_ns > a.idle_budget_ns) break;
+                __nanosleep(256);
+                continue;
+            }
+        }
+        long long r = 0, t0 = 0, m = 0;
+        if (lane == 0) {
+            r = q;
+            t0 = cn - qfirst;
+            m = (ce < qfirst + qnt ? ce : qfirst + qnt) - cn;
+        }
+        r = __shfl_sync(FULL, r, 0);
+        t0 = __shfl_sync(FULL, t0, 0);
+        m = __shfl_sync(FULL, m, 0);
+        idle_ns = 0;
+        __syncwarp();
         if (r != cached) {
             // the request's record, one 8-byte word per lane, read past L1 (a
-            // slot is rewritten for each request) and after the counter that
-            // announced it
+            // slot is rewritten for each request), after the acquire of total
             constexpr int kWords = (int)(sizeof(BatchOp) / 8) + 1;  // the op, then its kind
             static_assert(kWords <= 32, "record copied one word per lane");
-            const unsigned long long *src = reinterpret_cast<const unsigned long long *>(&dring[r & mask]);
+            const unsigned long long *src = reinterpret_cast<const unsigned long long *>(&a.dring[r & a.mask]);
             if (lane < kWords) {
                 const unsigned long long v = ld_relaxed_gpu(src + lane);
                 if (lane < kWords - 1) reinterpret_cast<unsigned long long *>(&wop[w])[lane] = v;
                 else wkind[w] = (int32_t)v;
             }
+            h = Hint{-1, 0};
+            cached = r;
         }
         __syncwarp();
-        if (r != cached) h = Hint{-1, 0};
-        cached = r;
-        if (wkind[w] == DTE_BATCH_PACK) serve_span_dir<true>(&wop[w], t, k, lane, scr, h);
-        else serve_span_dir<false>(&wop[w], t, k, lane, scr, h);
+        if (wkind[w] == DTE_BATCH_PACK) serve_span_dir<true>(&wop[w], t0, m, lane, scr, h);
+        else serve_span_dir<false>(&wop[w], t0, m, lane, scr, h);
         __threadfence();
         __syncwarp();
         if (lane == 0) {
-            const int64_t slot = r & mask;
-            const unsigned long long old = atomicAdd(done + slot, (unsigned long long)k);
-            if ((int64_t)old + k == wntiles[w]) {
-                done[slot] = 0;
+            const long long slot = r & a.mask;
+            const unsigned long long old = atomicAdd(a.done + slot, (unsigned long long)m);
+            if ((long long)old + m == qnt) {
                 __threadfence_system();
-                st_release_sys(comp + slot, r + 1);
+                st_release_sys(a.comp + slot, r + 1);
             }
+            cn += m;
         }
         __syncwarp();
     }
@@ -278,12 +437,14 @@ struct dte_server_s {
     cudaStream_t stream = nullptr;
     int64_t slots = 0, mask = 0, cap = 0;
     int ctas_per_sm = 2;
+    int sms = 1;
     int64_t span = 4;
     int64_t idle_limit = 0;
     SlotRec *ring = nullptr;  // pinned
     Ctrl *ctrl = nullptr;     // pinned
     int64_t *comp = nullptr;  // pinned, one per slot
-    char *dstate = nullptr;   // device: DevState, tile counters, done counters, mirrored records
+    char *dstate = nullptr;   // device: claim and publication lines, per-slot tiles, done counters,
+                              // mirrored records and per-warp held claims
     // host bookkeeping
     struct Pending {
         BatchOp op;
@@ -308,22 +469,51 @@ struct dte_server_s {
 
 namespace dte {
 
-static size_t dstate_bytes(int64_t slots)
+// Largest claim a warp takes at once (tiles); the smallest is the loop's
+// span_tiles setting.
+constexpr int64_t kServeSpanMax = 64;
+
+// Layout of the device state: ClaimLine | PubLine | SlotTile[slots] |
+// done[slots] | SlotRec[slots] | Held[warps].
+static size_t dstate_bytes(int64_t slots, int64_t warps)
 {
-    return sizeof(DevState) + (size_t)slots * (2 * sizeof(unsigned long long) + sizeof(SlotRec));
+    return sizeof(ClaimLine) + sizeof(PubLine) +
+           (size_t)slots * (sizeof(SlotTile) + sizeof(unsigned long long) + sizeof(SlotRec)) +
+           (size_t)warps * sizeof(Held);
 }
 
 static void server_launch(dte_server s)
 {
-    int sms = 1;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
-    DevState *st = reinterpret_cast<DevState *>(s->dstate);
-    unsigned long long *ctr = reinterpret_cast<unsigned long long *>(s->dstate + sizeof(DevState));
-    unsigned long long *done = ctr + s->slots;
-    SlotRec *dring = reinterpret_cast<SlotRec *>(done + s->slots);
+    ServeArgs a;
+    char *p = s->dstate;
+    a.claim = reinterpret_cast<ClaimLine *>(p);
+    p += sizeof(ClaimLine);
+    a.pub = reinterpret_cast<PubLine *>(p);
+    p += sizeof(PubLine);
+    a.stile = reinterpret_cast<SlotTile *>(p);
+    p += (size_t)s->slots * sizeof(SlotTile);
+    a.done = reinterpret_cast<unsigned long long *>(p);
+    p += (size_t)s->slots * sizeof(unsigned long long);
+    a.dring = reinterpret_cast<SlotRec *>(p);
+    p += (size_t)s->slots * sizeof(SlotRec);
+    a.held = reinterpret_cast<Held *>(p);
+    a.ring = s->ring;
+    a.ctrl = s->ctrl;
+    a.comp = s->comp;
+    a.mask = s->mask;
+    a.slots = s->slots;
+    a.span_min = s->span;
+    a.span_max = std::max<int64_t>(s->span, kServeSpanMax);
+    a.idle_budget_ns = s->idle_limit * 1000;
     __atomic_store_n(&s->ctrl->stop, (int64_t)0, __ATOMIC_RELEASE);
-    serve_kernel<<<(unsigned)(sms * s->ctas_per_sm), kThreads, 0, s->stream>>>(
-        s->ring, s->mask, s->ctrl, st, ctr, done, dring, s->comp, s->span, s->idle_limit * 1000);
+    // stream-ordered after the previous launch has ended
+    if (cudaMemsetAsync(&a.pub->mirror_gone, 0, sizeof(int), s->stream) != cudaSuccess) {
+        cudaGetLastError();
+        s->launched = false;
+        return;
+    }
+    // the grid is the same at every launch: held claims are per warp
+    serve_kernel<<<(unsigned)(s->sms * s->ctas_per_sm), kThreads, 0, s->stream>>>(a);
     s->launched = cudaGetLastError() == cudaSuccess;
 }
 
@@ -410,12 +600,18 @@ int dte_server_create(const dte_server_config *cfg, dte_server *out)
     s->span = c.span_tiles;
     s->idle_limit = c.idle_exit_us;
     s->slot.resize((size_t)s->slots);
+    if (cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || s->sms < 1) {
+        cudaGetLastError();
+        delete s;
+        return DTE_ERR_CUDA;
+    }
+    const int64_t warps = (int64_t)s->sms * s->ctas_per_sm * kWarps;
     bool ok = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) == cudaSuccess &&
               cudaHostAlloc(&s->ring, sizeof(SlotRec) * (size_t)s->slots, cudaHostAllocMapped) == cudaSuccess &&
               cudaHostAlloc(&s->ctrl, sizeof(Ctrl), cudaHostAllocMapped) == cudaSuccess &&
               cudaHostAlloc(&s->comp, sizeof(int64_t) * (size_t)s->slots, cudaHostAllocMapped) == cudaSuccess &&
-              cudaMalloc(&s->dstate, dstate_bytes(s->slots)) == cudaSuccess &&
-              cudaMemset(s->dstate, 0, dstate_bytes(s->slots)) == cudaSuccess;
+              cudaMalloc(&s->dstate, dstate_bytes(s->slots, warps)) == cudaSuccess &&
+              cudaMemset(s->dstate, 0, dstate_bytes(s->slots, warps)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         dte_server_free(&s);
@@ -451,7 +647,7 @@ int dte_server_submit(dte_server s, int kind, const dte_op *op, int64_t *ticket)
             int dev;
             if (int rc = device_blob(op->type, &dblob, &dev)) return rc;
             if (dev != s->device) return DTE_ERR_ARG;
-            fill_batch_op(p.op, *op->type->desc, op->type->extent(), *op, dblob);
+            fill_batch_op(p.op, *op->type->desc, op->type->extent(), *op, dblob, op->type->plan);
             p.ntiles = op_tiles(p.op);
             p.keep = op->type->desc;
         }

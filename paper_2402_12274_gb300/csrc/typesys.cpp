@@ -1101,6 +1101,7 @@ int dte_type_dup(dte_type old, dte_type *out)
     t->node = old->node;
     t->desc = old->desc;
     t->committed = old->committed;
+    t->plan = old->plan;
     register_handle(t);
     *out = t;
     return DTE_SUCCESS;
@@ -1178,6 +1179,23 @@ int dte_type_num_segments(dte_type t, int64_t *nseg)
     if (int rc = check_old(t)) return rc;
     if (!nseg) return DTE_ERR_ARG;
     *nseg = t->node->nseg;
+    return DTE_SUCCESS;
+}
+
+int dte_type_set_plan(dte_type t, int plan)
+{
+    if (int rc = check_old(t)) return rc;
+    if (t->predefined) return DTE_ERR_TYPE;
+    if (plan < DTE_PLAN_AUTO || plan > DTE_PLAN_BULK) return DTE_ERR_ARG;
+    t->plan = plan;
+    return DTE_SUCCESS;
+}
+
+int dte_type_get_plan(dte_type t, int *plan)
+{
+    if (int rc = check_old(t)) return rc;
+    if (!plan) return DTE_ERR_ARG;
+    *plan = t->plan;
     return DTE_SUCCESS;
 }
 

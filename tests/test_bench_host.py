@@ -71,3 +71,29 @@ def test_traffic_record_only_for_the_kernels_it_was_taken_on(monkeypatch):
 
 def test_job_throughput_counts_every_rank():
     assert bench.job_throughput(2e9, 4, 1.0) == 8.0
+
+
+def test_sector_floor_matches_a_byte_count_from_the_oracle():
+    # faces of a 16^3 float64 grid: the floor from the library's segment
+    # lists equals a byte-by-byte count over the oracle's typemaps
+    import numpy as np
+
+    import inputs
+    import oracle
+    import paper_2402_12274_gb300 as dte
+    n = 16
+    specs = inputs.halo_face_specs(n, 2)
+    faces = [dte.Datatype.from_spec(s).commit() for s in specs]
+    packed = sum(f.size for f in faces)
+    got = bench.sector_floor(faces, n ** 3 * 8, packed)
+    cov = np.zeros(n ** 3 * 8, bool)
+    for s in specs:
+        d, ln = oracle.from_spec(s).iov_elements(1)
+        for a, b in zip(d, ln):
+            cov[a:a + b] = True
+    per_sector = cov.reshape(-1, 32).sum(axis=1)
+    touched = int(np.count_nonzero(per_sector))
+    partial = int(np.count_nonzero((per_sector > 0) & (per_sector < 32)))
+    assert got["touched_sectors"] == touched and got["partial_sectors"] == partial
+    assert got["pack"] == 32 * touched + packed
+    assert got["unpack"] == packed + 32 * touched + 32 * partial
