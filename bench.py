@@ -847,7 +847,7 @@ def run_config_autograd(args):
                                             "backward_us": round(tb * 1e6, 1), "entries": t.size // 4})
 
 
-def serve_measure(nreq: int, rhos=(0.5, 0.8, 0.95), seed: int = 5, ctas_per_sm: int = 2):
+def serve_measure(nreq: int, rhos=(0.5, 0.8, 0.95), seed: int = 5, ctas_per_sm: int = 2, span_tiles: int = 8):
     """Request loop under Poisson arrivals: pack/unpack requests (50/50) of
     layouts from the batch generator with sizes log-uniform 1 KiB - 64 MiB,
     admission cap 8 GiB.  The service rate mu is measured first (all requests
@@ -874,7 +874,8 @@ def serve_measure(nreq: int, rhos=(0.5, 0.8, 0.95), seed: int = 5, ctas_per_sm: 
     picks = rng.integers(0, len(pool), nreq)
     kinds = rng.integers(0, 2, nreq)
     nbytes = np.array([2 * pool[i][0].size for i in picks], dtype=np.float64)
-    srv = dte.dte_server_create(ring_slots=1024, max_inflight_bytes=8 << 30, ctas_per_sm=ctas_per_sm)
+    srv = dte.dte_server_create(ring_slots=1024, max_inflight_bytes=8 << 30, ctas_per_sm=ctas_per_sm,
+                                span_tiles=span_tiles)
 
     def submit(i):
         t, u, p = pool[picks[i]]

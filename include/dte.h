@@ -483,7 +483,8 @@ typedef struct dte_server_config {
     int64_t max_inflight_bytes;  /* cap on moved bytes (2*count*size) of admitted, unfinished
                                     requests (default 8 GiB); a larger request is admitted alone */
     int32_t ctas_per_sm;         /* persistent CTAs per SM, 1 or 2 (default 2) */
-    int32_t span_tiles;          /* tiles (1-2 KiB, or 32-segment rounds) a warp claims at once (4) */
+    int32_t span_tiles;          /* fewest tiles (1-2 KiB, or 32-segment rounds) a warp claims at once;
+                                    claims grow to 64 while many published tiles are unclaimed (8) */
     int64_t idle_exit_us;        /* empty-poll budget before the loop leaves (default 50000) */
 } dte_server_config;
 

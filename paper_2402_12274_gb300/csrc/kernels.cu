@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_seg_kernel(const B
             const char *blob = soff >= 0 ? reinterpret_cast<const char *>(smem) + soff : b->d.blob;
             const DNode *nodes = reinterpret_cast<const DNode *>(blob + sizeof(BlobHeader));
             const int64_t base = (t - tile0[i]) * 32;
-            seg_round<W, PACK>(wop[wid], nodes, blob, b->nseg_elem, b->div_nseg, base, b->nsegs, lane, h, rh);
+            seg_round<W, PACK, false>(wop[wid], nodes, blob, b->nseg_elem, b->div_nseg, base, b->nsegs, lane, h, rh);
         }
     }
 }

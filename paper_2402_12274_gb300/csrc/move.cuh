@@ -443,8 +443,11 @@ __device__ __forceinline__ void shared_list_round(const Op &op, const DNode *nod
 }
 
 // One round: segments [base, base + 32) clipped to s1 (warp-uniform args).
-// `rh` is the warp's search position in a root index list.
-template <int W, bool PACK>
+// `rh` is the warp's search position in a root index list.  LISTDEC enables
+// the warp decode of shared-child root lists (the batch kernels leave it out:
+// under their 64-register budget the extra path costs the common layouts
+// more than it gives the rare index-of-struct ones).
+template <int W, bool PACK, bool LISTDEC = true>
 __device__ __forceinline__ void seg_round(const Op &op, const DNode *nodes, const char *blob, int64_t nseg_elem,
                                           const FastDiv &div_nseg, int64_t base, int64_t s1, int lane, Hint &h,
                                           Hint &rh)
@@ -456,7 +459,7 @@ __device__ __forceinline__ void seg_round(const Op &op, const DNode *nodes, cons
     const DNode &R = nodes[op.root];
     const int64_t e0 = fdiv(base, div_nseg);
     const int64_t local0 = base - e0 * nseg_elem;
-    if (shared_list_root(R) && local0 + nvalid <= nseg_elem) {
+    if (LISTDEC && shared_list_root(R) && local0 + nvalid <= nseg_elem) {
         shared_list_round(op, nodes, blob, R, e0, local0, nvalid, lane, rh, h, disp, len, ps);
     } else if (lane < nvalid) {
         const int64_t k = base + lane;

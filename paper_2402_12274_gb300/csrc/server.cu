@@ -215,13 +215,13 @@ constexpr int kServeCtas = DTE_SERVE_CTAS;  // most CTAs per SM the loop is comp
 // of that sequence with one fetch-add (which always succeeds: a
 // compare-and-swap claim fails whenever another claim lands between reading
 // the counter and swapping it, which at this claim rate is nearly always).  k
-// shrinks with the published tiles left unclaimed (guided self-scheduling:
-// about half of them spread over all warps, at most span_max, at least
-// span_min while many are left and 1 near the end), so a large request is
-// handed out in a few large claims and the last tiles of a burst one by one.
-// A claim may cover the ends of several requests, which are processed in
-// turn, and may run past the published total when warps race for the last
-// tiles (an over-claim, at most k tiles per warp): the warp keeps those tiles
+// follows the published tiles left unclaimed (guided self-scheduling: about
+// half of them spread over all warps) within [span_min, span_max]: a claim
+// costs a chain of dependent round trips, so it always takes enough tiles to
+// outweigh that, even when hungry warps keep the unclaimed backlog short.  A
+// claim may cover the ends of several requests, which are processed in turn,
+// and may run past the published total when warps race for the last tiles
+// (an over-claim, at most k tiles per warp): the warp keeps those tiles
 // and processes them once the requests they belong to are published.  Tiles
 // are never handed out twice (fetch-adds give disjoint ranges) and never
 // dropped: a warp gives up a range only by finishing it, and a warp that
@@ -323,8 +323,7 @@ __global__ void __launch_bounds__(kThreads, kServeCtas) serve_kernel(ServeArgs a
                 const long long G = (long long)ld_relaxed_gpu(&a.claim->next);
                 if (G < TT) {
                     long long k = (TT - G) / (2 * nwarps);
-                    const long long lo = TT - G >= a.span_min * nwarps ? a.span_min : 1;
-                    k = k < lo ? lo : k > a.span_max ? a.span_max : k;
+                    k = k < a.span_min ? a.span_min : k > a.span_max ? a.span_max : k;
                     cn = (long long)atomicAdd(&a.claim->next, (unsigned long long)k);
                     ce = cn + k;
                 }
@@ -580,7 +579,7 @@ extern "C" {
 int dte_server_create(const dte_server_config *cfg, dte_server *out)
 {
     if (!out) return DTE_ERR_ARG;
-    dte_server_config c{1024, (int64_t)8 << 30, 2, 4, 50000};
+    dte_server_config c{1024, (int64_t)8 << 30, 2, 8, 50000};
     if (cfg) c = *cfg;
     if (c.ring_slots <= 0 || (c.ring_slots & (c.ring_slots - 1)) || c.ring_slots > (1 << 20)) return DTE_ERR_ARG;
     if (c.max_inflight_bytes <= 0 || c.ctas_per_sm < 1 || c.ctas_per_sm > kServeCtas || c.span_tiles < 1 ||
