@@ -58,7 +58,7 @@ def parse():
                    help="skip the rest of the metric (large-block gate, batch vs per-call, serving loop)")
     p.add_argument("--config", default="halo",
                    help="halo (headline, default) | vector | records | batch | largeblock | autograd | serve | "
-                        "pipeline | faces | all")
+                        "pipeline | faces | fastaxis | all")
     p.add_argument("--records-blocks", type=int, default=1 << 22)
     p.add_argument("--batch-ops", type=int, default=10000)
     p.add_argument("--serve-requests", type=int, default=20000)
@@ -1064,9 +1064,57 @@ def run_config_faces(args):
            "note": "means of 100 CUDA-event timings (8.192 us event resolution), L2 flushed before each"})
 
 
+def run_config_fastaxis(args):
+    """The two halo faces normal to the fastest axis of the 512^3 float64
+    grid (2 x 262,144 runs of 16 bytes at a 4 KiB stride): their struct pack
+    (one move_kernel launch) and their unpack as a two-op batch (one
+    batch_kernel launch), eight of each, L2 flushed before every launch; the
+    sector floor of each beside the times."""
+    import torch
+    import paper_2402_12274_gb300 as dte
+    import inputs
+    dev = torch.device("cuda", 0)
+    s = torch.cuda.Stream()
+    fl = L2Flush(dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(2)
+    grid = torch.randn(N ** 3, dtype=torch.float64, device=dev, generator=gen)
+    grid2 = torch.zeros_like(grid)
+    specs = inputs.halo_face_specs(N, G)[4:6]
+    faces = [dte.Datatype.from_spec(f).commit() for f in specs]
+    send = dte.Datatype.from_spec(inputs.all_faces_struct(specs)).commit()
+    packed = torch.empty(send.size, dtype=torch.uint8, device=dev)
+    b2 = dte.Batch(dte.BATCH_UNPACK, [(faces[0].h, 1, grid2.data_ptr(), packed.data_ptr()),
+                                      (faces[1].h, 1, grid2.data_ptr(), packed.data_ptr() + faces[0].size)])
+    ev = []
+    with torch.cuda.stream(s):
+        for _ in range(8):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            fl.zero_()
+            e[0].record(s)
+            dte.dte_pack_enqueue(grid.data_ptr(), 1, send.h, packed.data_ptr(), send.size, 0, s.cuda_stream)
+            e[1].record(s)
+            fl.zero_()
+            e[2].record(s)
+            b2.enqueue(s.cuda_stream)
+            e[3].record(s)
+            ev.append(e)
+    s.synchronize()
+    tp = float(np.mean([e[0].elapsed_time(e[1]) for e in ev[3:]])) * 1e-3
+    tu = float(np.mean([e[2].elapsed_time(e[3]) for e in ev[3:]])) * 1e-3
+    floor = sector_floor(faces, N ** 3 * 8, send.size)
+    peak, _ = peaks()
+    _line("512^3 float64 halo faces normal to the fastest axis (16-byte runs at a 4 KiB stride)",
+          "two-face pack+unpack us", round((tp + tu) * 1e6, 2), "us",
+          {"higher_is_better": False, "pack_us": round(tp * 1e6, 2), "unpack_us": round(tu * 1e6, 2),
+           "floor_bytes": {"pack": floor["pack"], "unpack": floor["unpack"]},
+           "frac_of_floor": {"pack": round(floor["pack"] / tp / 1e9 / peak, 4),
+                             "unpack": round(floor["unpack"] / tu / 1e9 / peak, 4)}})
+
+
 CONFIGS = {"vector": run_config_vector, "records": run_config_records, "batch": run_config_batch,
            "largeblock": run_config_largeblock, "autograd": run_config_autograd, "serve": run_config_serve,
-           "pipeline": run_config_pipeline, "faces": run_config_faces}
+           "pipeline": run_config_pipeline, "faces": run_config_faces, "fastaxis": run_config_fastaxis}
 
 
 def main():

@@ -435,10 +435,24 @@ __device__ __forceinline__ void shared_list_round(const Op &op, const DNode *nod
     if (lane < nvalid) {
         const int64_t local = local0 + lane - se;
         const int64_t i = fdiv(local, C.div_nseg);
+        const int64_t j = local - i * C.nseg;
         disp = e0 * op.extent + R.base + de + i * R.stride;
-        int64_t pc;
-        decode_seg(nodes, blob, R.child, local - i * C.nseg, disp, len, pc, h);
-        ps = e0 * op.esize + pbe + i * C.size + pc;
+        ps = e0 * op.esize + pbe + i * C.size;
+        if (C.kind == NK_LIST && (C.flags & NF_RUNS)) {
+            // a child that is a table of runs (a struct of basic blocks):
+            // run j directly
+            const int64_t *cp = arr<int64_t>(blob, C.a_pbytes);
+            disp += C.base + arr<int64_t>(blob, C.a_disp)[j];
+            ps += cp[j];
+            len = cp[j + 1] - cp[j];
+        } else if (C.kind == NK_RUN) {
+            disp += C.base;
+            len = C.len;
+        } else {
+            int64_t pc;
+            decode_seg(nodes, blob, R.child, j, disp, len, pc, h);
+            ps += pc;
+        }
     }
 }
 
@@ -472,6 +486,31 @@ __device__ __forceinline__ void seg_round(const Op &op, const DNode *nodes, cons
     // (a range move may start or end inside a segment)
     const int64_t p0 = max(__shfl_sync(FULL, ps, 0), op.pbase);
     const int64_t p1 = min(__shfl_sync(FULL, ps + len, nvalid - 1), op.pbase + op.total);
+    // Rounds whose runs are balanced (the longest at most four times the
+    // mean) move run by run: each lane copies its own run in W-byte words,
+    // four loads in flight.  That costs a few instructions per word where the
+    // cooperative loop below pays a segment lookup per word; a round with one
+    // run much longer than the rest keeps the cooperative loop, which spreads
+    // the round's bytes (not its runs) over the lanes.
+    const unsigned maxlen = __reduce_max_sync(FULL, (unsigned)len);  // runs are <= kSegMaxRun
+    if ((int64_t)maxlen * nvalid <= 4 * (p1 - p0)) {
+        if (lane < nvalid) {
+            const int64_t a = max(ps, p0), e = min(ps + len, p1);
+            const char *src = PACK ? op.user_in + disp + (a - ps) : op.packed_in - op.pbase + a;
+            char *dst = PACK ? op.packed_out - op.pbase + a : op.user_out + disp + (a - ps);
+            const int n = (int)(e - a);
+            for (int o = 0; o < n; o += 4 * W) {
+                T v[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (o + u * W < n) v[u] = ldw<W>(src + o + u * W);
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (o + u * W < n) stw<W>(dst + o + u * W, v[u]);
+            }
+        }
+        return;
+    }
     const int64_t nwords = (p1 - p0) / W;
     const char *pk_in = op.packed_in - op.pbase;  // indexed by stream offset
     char *pk_out = op.packed_out - op.pbase;
