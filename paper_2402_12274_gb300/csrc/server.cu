@@ -75,14 +75,19 @@ __device__ __forceinline__ void st_release_sys(int64_t *p, int64_t v)
 // One claimed span of tiles [t, t + k) of a request, out of line (one copy of
 // each variant for the whole loop, one call per claim).  The search hint h
 // is the warp's, kept while it works on the same request, so consecutive
-// tiles of a large index table continue the search where it stopped.
+// tiles of a large index table continue the search where it stopped.  The
+// spans work on a copy of it in registers: a hint reached through the
+// reference would live in local memory, and every descriptor walk reads and
+// writes it.
 template <int W, bool PACK, bool PK16, bool WIDE = false>
 __device__ __noinline__ void serve_chunk_span(const BatchOp *b, int64_t t, int64_t k, int lane, char *scr, Hint &h)
 {
     const char *blob = b->d.blob;
     const DNode *nodes = reinterpret_cast<const DNode *>(blob + sizeof(BlobHeader));
+    Hint hr = h;
     for (int64_t tt = t; tt < t + k; tt++)
-        warp_step<W, PACK, PK16, WIDE>(b->op, nodes, blob, tt * kStepOf<W, WIDE>, b->nchunks, lane, h, scr);
+        warp_step<W, PACK, PK16, WIDE>(b->op, nodes, blob, tt * kStepOf<W, WIDE>, b->nchunks, lane, hr, scr);
+    h = hr;
 }
 
 template <int W, bool PACK>
@@ -90,9 +95,10 @@ __device__ __noinline__ void serve_seg_span(const BatchOp *b, int64_t t, int64_t
 {
     const char *blob = b->d.blob;
     const DNode *nodes = reinterpret_cast<const DNode *>(blob + sizeof(BlobHeader));
-    Hint rh{-1, 0};
+    Hint hr = h, rh{-1, 0};
     for (int64_t tt = t; tt < t + k; tt++)
-        seg_round<W, PACK>(b->op, nodes, blob, b->nseg_elem, b->div_nseg, tt * 32, b->nsegs, lane, h, rh);
+        seg_round<W, PACK>(b->op, nodes, blob, b->nseg_elem, b->div_nseg, tt * 32, b->nsegs, lane, hr, rh);
+    h = hr;
 }
 
 template <bool PACK>
@@ -238,6 +244,25 @@ __global__ void __launch_bounds__(kThreads, kServeCtas) serve_kernel(ServeArgs a
     const int w = threadIdx.x >> 5;
     const bool mirror = blockIdx.x == 0 && w == 0;
     const long long nwarps = (long long)gridDim.x * kWarps - 1;  // claiming warps
+    // Idle warps of a CTA do not all poll the global words: one scout warp
+    // per CTA does, and the others sleep on the CTA's epoch in shared memory,
+    // which any warp of the CTA bumps when it sees the published total move.
+    // (Thousands of warps polling one line with acquire loads saturate its L2
+    // slice, and every claim, fence and completion that goes there queues
+    // behind the polls.)
+    __shared__ unsigned cta_epoch;
+    __shared__ long long cta_total;  // the published total the CTA last saw
+    __shared__ int cta_leave;        // the scout has left: the CTA's warps leave
+    if (threadIdx.x == 0) {
+        cta_epoch = 0;
+        cta_total = 0;
+        cta_leave = 0;
+    }
+    __syncthreads();
+    const bool scout = w == (blockIdx.x == 0 ? 1 : 0);
+    volatile unsigned *vepoch = &cta_epoch;
+    volatile long long *vtotal = &cta_total;
+    volatile int *vleave = &cta_leave;
     int64_t idle_ns = 0;
     unsigned backoff = 128;
     if (mirror) {
@@ -315,10 +340,17 @@ __global__ void __launch_bounds__(kThreads, kServeCtas) serve_kernel(ServeArgs a
     }
     int64_t cached = -1;  // request whose record is in wop[w]
     Hint h{-1, 0};        // search position in that request's descriptor
+    unsigned ep = 0;  // lane 0: the CTA's epoch before its last look at the total
     for (;;) {
         int have = 0;
         if (lane == 0) {
+            ep = *vepoch;
+            __threadfence_block();
             const long long TT = (long long)ld_acquire_gpu(&a.pub->total);
+            if (TT != *vtotal) {  // wake the CTA's sleeping warps
+                *vtotal = TT;
+                atomicAdd(&cta_epoch, 1u);
+            }
             if (cn >= ce) {
                 const long long G = (long long)ld_relaxed_gpu(&a.claim->next);
                 if (G < TT) {
@@ -335,19 +367,47 @@ __global__ void __launch_bounds__(kThreads, kServeCtas) serve_kernel(ServeArgs a
             // tiles); leave on stop, when the mirroring warp has left (nothing
             // more is published in this launch), or after the idle budget --
             // keeping any claim for the same warp of the next launch
+            if (scout) {
+                if (lane == 0) {
+                    int gone;
+                    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(gone) : "l"(&a.pub->mirror_gone) : "memory");
+                    have = gone || ld_relaxed_sys(&a.ctrl->stop) != 0;
+                }
+                idle_ns += backoff;
+                if (__shfl_sync(FULL, have, 0) || idle_ns > a.idle_budget_ns) {
+                    if (lane == 0) {
+                        if (cn < ce) a.held[gw] = Held{cn, ce};
+                        *vleave = 1;
+                    }
+                    break;
+                }
+                __nanosleep(backoff);
+                const unsigned cap = __shfl_sync(FULL, (int)(cn < ce), 0) ? 512u : 2048u;
+                backoff = backoff < cap ? backoff * 2 : cap;
+                continue;
+            }
+            // the other warps sleep until the CTA's epoch moves past the one
+            // seen before their look at the total (bounded like the scout)
+            int leave = 0;
             if (lane == 0) {
-                int gone;
-                asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(gone) : "l"(&a.pub->mirror_gone) : "memory");
-                have = gone || ld_relaxed_sys(&a.ctrl->stop) != 0;
+                for (;;) {
+                    if (*vleave) {
+                        leave = 1;
+                        break;
+                    }
+                    if (*vepoch != ep) break;
+                    idle_ns += backoff;
+                    if (idle_ns > a.idle_budget_ns) {
+                        leave = 1;
+                        break;
+                    }
+                    __nanosleep(backoff);
+                    backoff = backoff < 1024u ? backoff * 2 : 1024u;
+                }
+                if (leave && cn < ce) a.held[gw] = Held{cn, ce};
             }
-            idle_ns += backoff;
-            if (__shfl_sync(FULL, have, 0) || idle_ns > a.idle_budget_ns) {
-                if (lane == 0 && cn < ce) a.held[gw] = Held{cn, ce};
-                break;
-            }
-            __nanosleep(backoff);
-            const unsigned cap = __shfl_sync(FULL, (int)(cn < ce), 0) ? 512u : 2048u;
-            backoff = backoff < cap ? backoff * 2 : cap;
+            if (__shfl_sync(FULL, leave, 0)) break;
+            idle_ns = __shfl_sync(FULL, idle_ns, 0);
             continue;
         }
         backoff = 128;
