@@ -97,3 +97,9 @@ def test_sector_floor_matches_a_byte_count_from_the_oracle():
     assert got["touched_sectors"] == touched and got["partial_sectors"] == partial
     assert got["pack"] == 32 * touched + packed
     assert got["unpack"] == packed + 32 * touched + 32 * partial
+
+
+def test_csrc_hash_covers_every_kernel_source_but_the_request_loop():
+    import os
+    d = os.path.join(bench.ROOT, "paper_2402_12274_gb300", "csrc")
+    assert set(bench.KERNEL_SOURCES) == set(os.listdir(d)) - {"server.cu"}
