@@ -17,8 +17,8 @@
 //                                          claim ranges of it with one
 //                                          fetch-add on a single counter,
 //                                          sized by the tiles still unclaimed
-//   progress: read completion words        the warp that finishes a request's
-//   (acquire), free capacity, admit more   last tile writes its completion word
+//   progress: read the completion queue    the warp that finishes a request's
+//   (acquire), free capacity, admit more   last tile appends it to the queue
 //
 // Every device wait is bounded: a warp that finds nothing to do polls with
 // __nanosleep and leaves after `idle_limit` of empty polls (a claim it still
@@ -154,11 +154,15 @@ struct SlotTile {              // where a mirrored request's tiles start
 struct Held {                  // a warp's claim, kept across launches of the loop
     long long next, end;
 };
+struct alignas(128) CqLine {
+    unsigned long long tail;   // completion-queue positions handed out
+};
 
 struct ServeArgs {
     const SlotRec *ring;       // pinned host ring of admitted requests
     Ctrl *ctrl;                // pinned host control words
-    int64_t *comp;             // pinned completion words, one per slot
+    int64_t *cq;               // pinned completion queue, one entry per slot: request + 1, or 0
+    unsigned long long *cq_tail;  // device: completions so far (positions handed out)
     ClaimLine *claim;
     PubLine *pub;
     SlotTile *stile;           // per slot
@@ -207,6 +211,19 @@ __device__ __forceinline__ long long request_of_tile(const ServeArgs &a, long lo
         hi = min(lo + step, hi);
     }
     return lo;
+}
+
+// Announce request r as complete: append r + 1 to the completion queue at the
+// next position.  The host reads the queue in position order and clears what
+// it read; positions cannot lap an entry the host has not read (every
+// completion belongs to an admitted request, and the host admits a request
+// only into a slot it retired through the queue, so completions never exceed
+// the host's reads by more than the ring's size).
+__device__ __forceinline__ void complete_request(const ServeArgs &a, long long r)
+{
+    __threadfence_system();
+    const unsigned long long pos = atomicAdd(a.cq_tail, 1ull);
+    st_release_sys(a.cq + (long long)(pos & (unsigned long long)a.mask), r + 1);
 }
 
 #ifndef DTE_SERVE_CTAS
@@ -311,10 +328,7 @@ __global__ void __launch_bounds__(kThreads, kServeCtas) serve_kernel(ServeArgs a
                     a.stile[slot].tag = qq;
                     asm volatile("st.release.gpu.global.s64 [%0], %1;" ::"l"(&a.stile[slot].first), "l"(tt)
                                  : "memory");
-                    if (nt == 0) {  // nothing to move: complete at once
-                        __threadfence_system();
-                        st_release_sys(a.comp + slot, qq + 1);
-                    }
+                    if (nt == 0) complete_request(a, qq);  // nothing to move: complete at once
                     tt += nt;
                 }
                 __threadfence();
@@ -477,10 +491,7 @@ __global__ void __launch_bounds__(kThreads, kServeCtas) serve_kernel(ServeArgs a
         if (lane == 0) {
             const long long slot = r & a.mask;
             const unsigned long long old = atomicAdd(a.done + slot, (unsigned long long)m);
-            if ((long long)old + m == qnt) {
-                __threadfence_system();
-                st_release_sys(a.comp + slot, r + 1);
-            }
+            if ((long long)old + m == qnt) complete_request(a, r);
             cn += m;
         }
         __syncwarp();
@@ -501,7 +512,8 @@ struct dte_server_s {
     int64_t idle_limit = 0;
     SlotRec *ring = nullptr;  // pinned
     Ctrl *ctrl = nullptr;     // pinned
-    int64_t *comp = nullptr;  // pinned, one per slot
+    int64_t *cq = nullptr;    // pinned completion queue, one entry per slot
+    int64_t cq_head = 0;      // next completion-queue position to read
     char *dstate = nullptr;   // device: claim and publication lines, per-slot tiles, done counters,
                               // mirrored records and per-warp held claims
     // host bookkeeping
@@ -521,9 +533,9 @@ struct dte_server_s {
     std::vector<Slot> slot;
     int64_t next_req = 0;       // next request index to publish
     int64_t next_ticket = 0;    // tickets are handed out in submission order
-    int64_t oldest_open = 0;    // no request below this is still open
     int64_t inflight_bytes = 0, inflight = 0;
     bool launched = false;
+    int64_t last_query_ns = 0;  // when the runtime was last asked whether the loop runs
 };
 
 namespace dte {
@@ -532,11 +544,11 @@ namespace dte {
 // span_tiles setting.
 constexpr int64_t kServeSpanMax = 64;
 
-// Layout of the device state: ClaimLine | PubLine | SlotTile[slots] |
+// Layout of the device state: ClaimLine | PubLine | CqLine | SlotTile[slots] |
 // done[slots] | SlotRec[slots] | Held[warps].
 static size_t dstate_bytes(int64_t slots, int64_t warps)
 {
-    return sizeof(ClaimLine) + sizeof(PubLine) +
+    return sizeof(ClaimLine) + sizeof(PubLine) + sizeof(CqLine) +
            (size_t)slots * (sizeof(SlotTile) + sizeof(unsigned long long) + sizeof(SlotRec)) +
            (size_t)warps * sizeof(Held);
 }
@@ -549,6 +561,8 @@ static void server_launch(dte_server s)
     p += sizeof(ClaimLine);
     a.pub = reinterpret_cast<PubLine *>(p);
     p += sizeof(PubLine);
+    a.cq_tail = &reinterpret_cast<CqLine *>(p)->tail;
+    p += sizeof(CqLine);
     a.stile = reinterpret_cast<SlotTile *>(p);
     p += (size_t)s->slots * sizeof(SlotTile);
     a.done = reinterpret_cast<unsigned long long *>(p);
@@ -558,7 +572,7 @@ static void server_launch(dte_server s)
     a.held = reinterpret_cast<Held *>(p);
     a.ring = s->ring;
     a.ctrl = s->ctrl;
-    a.comp = s->comp;
+    a.cq = s->cq;
     a.mask = s->mask;
     a.slots = s->slots;
     a.span_min = s->span;
@@ -577,20 +591,24 @@ static void server_launch(dte_server s)
 }
 
 // Account completions, admit queued requests, and make sure the loop runs.
+// Completions are read from the queue the device appends to, so a call costs
+// the requests completed since the last one, not the requests in flight.
 static int server_progress(dte_server s)
 {
-    // completions (completion words are written in any order)
-    for (int64_t r = s->oldest_open; r < s->next_req; r++) {
-        dte_server_s::Slot &sl = s->slot[(size_t)(r & s->mask)];
-        if (!sl.open || sl.req != r) continue;
-        if (__atomic_load_n(s->comp + (r & s->mask), __ATOMIC_ACQUIRE) == r + 1) {
+    for (;;) {
+        int64_t *e = s->cq + (s->cq_head & s->mask);
+        const int64_t v = __atomic_load_n(e, __ATOMIC_ACQUIRE);
+        if (v == 0) break;
+        dte_server_s::Slot &sl = s->slot[(size_t)((v - 1) & s->mask)];
+        if (sl.open && sl.req == v - 1) {
             sl.open = false;
             sl.keep.reset();
             s->inflight_bytes -= sl.bytes;
             s->inflight--;
         }
+        __atomic_store_n(e, (int64_t)0, __ATOMIC_RELAXED);
+        s->cq_head++;
     }
-    while (s->oldest_open < s->next_req && !s->slot[(size_t)(s->oldest_open & s->mask)].open) s->oldest_open++;
     // admissions, in submission order
     while (!s->pending.empty()) {
         dte_server_s::Pending &p = s->pending.front();
@@ -612,13 +630,21 @@ static int server_progress(dte_server s)
         __atomic_store_n(&s->ctrl->published, s->next_req, __ATOMIC_RELEASE);
         s->pending.pop_front();
     }
-    // (re)start the loop if it left while work is outstanding
+    // (re)start the loop if it left while work is outstanding; whether it is
+    // still running is asked of the runtime at most every 20 us (the loop
+    // only leaves after idle_exit_us without work)
     if (s->inflight > 0) {
-        bool running = s->launched && cudaStreamQuery(s->stream) == cudaErrorNotReady;
-        if (!running) {
-            cudaGetLastError();
-            server_launch(s);
-            if (!s->launched) return DTE_ERR_CUDA;
+        const int64_t now = std::chrono::duration_cast<std::chrono::nanoseconds>(
+                                std::chrono::steady_clock::now().time_since_epoch())
+                                .count();
+        if (!s->launched || now - s->last_query_ns > 20000) {
+            s->last_query_ns = now;
+            bool running = s->launched && cudaStreamQuery(s->stream) == cudaErrorNotReady;
+            if (!running) {
+                cudaGetLastError();
+                server_launch(s);
+                if (!s->launched) return DTE_ERR_CUDA;
+            }
         }
     }
     return DTE_SUCCESS;
@@ -668,7 +694,7 @@ int dte_server_create(const dte_server_config *cfg, dte_server *out)
     bool ok = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) == cudaSuccess &&
               cudaHostAlloc(&s->ring, sizeof(SlotRec) * (size_t)s->slots, cudaHostAllocMapped) == cudaSuccess &&
               cudaHostAlloc(&s->ctrl, sizeof(Ctrl), cudaHostAllocMapped) == cudaSuccess &&
-              cudaHostAlloc(&s->comp, sizeof(int64_t) * (size_t)s->slots, cudaHostAllocMapped) == cudaSuccess &&
+              cudaHostAlloc(&s->cq, sizeof(int64_t) * (size_t)s->slots, cudaHostAllocMapped) == cudaSuccess &&
               cudaMalloc(&s->dstate, dstate_bytes(s->slots, warps)) == cudaSuccess &&
               cudaMemset(s->dstate, 0, dstate_bytes(s->slots, warps)) == cudaSuccess;
     if (!ok) {
@@ -678,7 +704,7 @@ int dte_server_create(const dte_server_config *cfg, dte_server *out)
     }
     std::memset(s->ring, 0, sizeof(SlotRec) * (size_t)s->slots);
     std::memset(s->ctrl, 0, sizeof(Ctrl));
-    std::memset(s->comp, 0, sizeof(int64_t) * (size_t)s->slots);
+    std::memset(s->cq, 0, sizeof(int64_t) * (size_t)s->slots);
     *out = s;
     return DTE_SUCCESS;
 }
@@ -759,7 +785,7 @@ int dte_server_free(dte_server *sp)
     if (s->stream) cudaStreamDestroy(s->stream);
     if (s->ring) cudaFreeHost(s->ring);
     if (s->ctrl) cudaFreeHost(s->ctrl);
-    if (s->comp) cudaFreeHost(s->comp);
+    if (s->cq) cudaFreeHost(s->cq);
     if (s->dstate) cudaFree(s->dstate);
     delete s;
     *sp = nullptr;
