@@ -470,7 +470,9 @@ DTE_API int dte_device_timeouts(int64_t *count);
  * requests as the host admits them, so requests of mixed sizes that arrive
  * while others are running are batched continuously instead of launched one
  * by one.  Admission is first-come first-served under a byte cap and a ring
- * of device slots.  Requests run without stream ordering: their inputs must
+ * of device slots.  On the device, requests are queued by direction and
+ * kernel variant, and the loop's warps drain one such group at a time, so
+ * requests admitted together may finish out of submission order.  Requests run without stream ordering: their inputs must
  * be ready (e.g. the producing stream synchronised) when submitted, and
  * their buffers and types must stay valid until they complete.  The loop
  * leaves after `idle_exit_us` without work and is relaunched by the next
@@ -483,8 +485,9 @@ typedef struct dte_server_config {
     int64_t max_inflight_bytes;  /* cap on moved bytes (2*count*size) of admitted, unfinished
                                     requests (default 8 GiB); a larger request is admitted alone */
     int32_t ctas_per_sm;         /* persistent CTAs per SM, 1 or 2 (default 2) */
-    int32_t span_tiles;          /* fewest tiles (1-2 KiB, or 32-segment rounds) a warp claims at once;
-                                    claims grow to 64 while many published tiles are unclaimed (8) */
+    int32_t span_tiles;          /* fewest tiles (1-2 KiB, or 32-segment rounds) a warp claims at once,
+                                    1..65536; claims grow to 64 while many published tiles are
+                                    unclaimed (default 8) */
     int64_t idle_exit_us;        /* empty-poll budget before the loop leaves (default 50000) */
 } dte_server_config;
 
@@ -496,7 +499,8 @@ DTE_API int dte_server_create(const dte_server_config *cfg, dte_server *out);
 /* Queue one request (kind DTE_BATCH_PACK or DTE_BATCH_UNPACK, one dte_op) and
  * return its ticket (tickets count up from 0 in submission order).  Admits it
  * at once if capacity allows, else keeps it queued on the host.  Never
- * blocks.  Unpack requests into an overlapping layout: DTE_ERR_OVERLAP. */
+ * blocks.  Unpack requests into an overlapping layout: DTE_ERR_OVERLAP; a
+ * request of more than 2^30 tiles: DTE_ERR_UNSUPPORTED. */
 DTE_API int dte_server_submit(dte_server s, int kind, const dte_op *op, int64_t *ticket);
 
 /* Account completions, admit queued requests, relaunch the loop if needed;

@@ -13,22 +13,26 @@
 //   submit -> FIFO; admit while ring       one warp mirrors newly published
 //   slots and the byte cap allow: write    requests into device memory and
 //   the record, then publish (release)     appends their tiles to one global
-//                                          tile sequence; the other warps
-//                                          claim ranges of it with one
-//                                          fetch-add on a single counter,
+//                                          tile sequence: at once while its
+//                                          unclaimed backlog is short, else
+//                                          from per-variant queues, one
+//                                          variant at a time; the other warps
+//                                          claim ranges of the sequence with
+//                                          one fetch-add on a single counter,
 //                                          sized by the tiles still unclaimed
 //   progress: read the completion queue    the warp that finishes a request's
 //   (acquire), free capacity, admit more   last tile appends it to the queue
 //
 // Every device wait is bounded: a warp that finds nothing to do polls with
 // __nanosleep and leaves after `idle_limit` of empty polls (a claim it still
-// holds is kept in device memory for the same warp of the next launch); the
-// host relaunches the loop when work arrives after it left.  A host stop flag
-// ends it at once.
+// holds is kept in device memory for the same warp of the next launch, and so
+// are the mirroring warp's queues); the host relaunches the loop while
+// requests are outstanding.  A host stop flag ends it at once.
 #include <cuda_runtime.h>
 
 #include <atomic>
 #include <chrono>
+#include <climits>
 #include <deque>
 #include <vector>
 
@@ -50,8 +54,6 @@ struct Ctrl {          // pinned host control block
     int64_t pad_[6];
 };
 
-constexpr int kTagBits = 36;  // tile counter = request << 36 | tile
-constexpr unsigned long long kTileMask = (1ull << kTagBits) - 1;
 
 __device__ __forceinline__ int64_t ld_acquire_sys(const int64_t *p)
 {
@@ -143,13 +145,22 @@ struct alignas(128) ClaimLine {
     unsigned long long next;   // next unclaimed tile of the global sequence
 };
 struct alignas(128) PubLine {
-    unsigned long long total;  // tiles of all mirrored requests (the sequence's length)
-    unsigned long long dpub;   // requests mirrored into device memory
+    unsigned long long total;  // tiles of all appended requests (the sequence's length)
+    unsigned long long apub;   // requests appended to the sequence
+    unsigned long long mirrored;  // requests copied into device memory (the mirroring warp's own)
     int mirror_gone;           // the mirroring warp has left (reset before each launch)
 };
-struct SlotTile {              // where a mirrored request's tiles start
-    long long tag;             // the request number (slots are reused)
+struct AppendEnt {             // the request appended at position p (entry p % slots)
+    long long tag;             // p (an entry is rewritten for p + slots)
     long long first;           // its first tile in the global sequence
+    long long req;             // the request
+    long long pad_;
+};
+struct QEnt {                  // a request waiting in the reorder stage
+    long long req, nt;
+};
+struct alignas(128) MirrorState {  // the reorder stage's queues between launches
+    long long qh[32], qt[32];
 };
 struct Held {                  // a warp's claim, kept across launches of the loop
     long long next, end;
@@ -165,27 +176,31 @@ struct ServeArgs {
     unsigned long long *cq_tail;  // device: completions so far (positions handed out)
     ClaimLine *claim;
     PubLine *pub;
-    SlotTile *stile;           // per slot
+    AppendEnt *alist;          // per append position modulo slots
+    QEnt *gq;                  // per group, `slots` entries: requests waiting to be appended
+    MirrorState *mstate;
+    long long *sreq;           // per slot: the request last mirrored into it
     unsigned long long *done;  // per slot: tiles finished
     SlotRec *dring;            // per slot: mirrored record
     Held *held;                // per warp of the grid
     int64_t mask, slots;
     int64_t span_min, span_max;
+    int64_t backlog_target;    // unclaimed tiles above which requests wait to be appended
     int64_t idle_budget_ns;
 };
 
-// Which mirrored request holds global tile c (c < total, read after the
-// acquire of total), searched by the whole warp.  Requests [dpub - slots,
-// dpub) sit in their slots unless they completed and the host reused the
-// slot; a reused slot belongs to a request older than c's (the host admits in
-// order and reuses a slot only after its request completed, and c's request
-// has not), so a slot whose tag is not its request number counts as "starts
-// at or before c".  The predicate "starts at or before c" is then true for
-// every request up to c's and false after it.  `lo` satisfies it.  Each pass
-// probes 32 evenly spaced requests of [lo, hi) at once and keeps the stretch
-// after the last one that satisfies it: two passes for a ring of 1024 slots.
-// Requests without tiles share their successor's first tile and are passed
-// over.  Returns -1 if lo itself fails (never expected: the caller retries).
+// The append position of the request holding global tile c (c < total, read
+// after the acquire of total), searched by the whole warp.  Positions [apub -
+// slots, apub) hold their entries unless the mirroring warp rewrote one for a
+// later append, which it does only after the entry's request completed: such
+// an entry belongs to a request appended before c's (c's request has not
+// completed, so its entry and every later one are intact), so an entry whose
+// tag is not its position counts as "starts at or before c".  The predicate
+// "starts at or before c" is then true for every position up to c's request
+// and false after it.  `lo` satisfies it.  Each pass probes 32 evenly spaced
+// positions of [lo, hi) at once and keeps the stretch after the last one that
+// satisfies it: two passes for a ring of 1024 slots.  Returns -1 if lo itself
+// fails (never expected: the caller retries).
 __device__ __forceinline__ long long request_of_tile(const ServeArgs &a, long long lo, long long hi, long long c,
                                                      int lane)
 {
@@ -195,7 +210,7 @@ __device__ __forceinline__ long long request_of_tile(const ServeArgs &a, long lo
         const long long p = lo + (long long)lane * step;
         bool starts_before = false;
         if (p < hi) {
-            const SlotTile *st = a.stile + (p & a.mask);
+            const AppendEnt *st = a.alist + (p & a.mask);
             // first is published with a release after tag: acquiring it orders
             // the tag read after it, so a tag that still matches goes with its
             // own first
@@ -231,10 +246,210 @@ __device__ __forceinline__ void complete_request(const ServeArgs &a, long long r
 #endif
 constexpr int kServeCtas = DTE_SERVE_CTAS;  // most CTAs per SM the loop is compiled for
 
-// The mirroring warp (warp 0 of CTA 0) does nothing else: it polls the host's
-// publication count, copies new records from pinned host memory into device
-// memory, gives each request its range of the global tile sequence, and then
-// publishes the new total.  Every other warp claims ranges [next, next + k)
+// Requests wait in the mirroring warp's reorder stage in groups that share a
+// kernel variant: direction x word class.
+constexpr int kGroups = 2 * kNumClasses;
+static_assert(kGroups <= 32, "one group per lane of a warp");
+
+__host__ __device__ constexpr int group_of(int kind, int wsel)
+{
+    return (kind == DTE_BATCH_PACK ? 0 : kNumClasses) + wsel;
+}
+
+// The mirroring warp (warp 0 of CTA 0).  It polls the host's publication
+// count, copies new records from pinned host memory into device memory, and
+// queues each request by group.  It appends queued requests to the global
+// tile sequence while the sequence's unclaimed backlog is below the target:
+// at moderate load every request is appended as soon as it is mirrored, in
+// admission order; once work piles up, the backlog stays near the target and
+// the requests behind it are appended group by group, so the warps claiming
+// consecutive tiles run the same kernel variant (interleaving variants on
+// the same SMs halves the loop's throughput).  It keeps appending the
+// current group while that group has requests queued and its quota (the
+// target again, in tiles) lasts, then switches to the group whose queued
+// request is oldest: no request waits behind more than one quota of every
+// other group.
+//
+// Append position p's entry is rewritten for p + slots only after the
+// request appended at p completed (checked before each append: its ring slot
+// now holds a later request, or all its tiles are done), so a warp looking up
+// a tile of an incomplete request always finds its entry.
+__device__ __forceinline__ void serve_mirror(const ServeArgs &a, int lane)
+{
+    const unsigned FULL = 0xffffffffu;
+    int64_t idle_ns = 0;
+    unsigned backoff = 128;
+    // this warp is the only writer of these counts: it reads them once (past
+    // L1) and keeps them in registers; a plain load could return a stale L1
+    // copy of a word that the atomics below update in L2
+    long long from = (long long)ld_relaxed_gpu(&a.pub->mirrored);
+    long long ap = (long long)ld_relaxed_gpu(&a.pub->apub);
+    long long tt = (long long)ld_relaxed_gpu(&a.pub->total);
+    // lane g < kGroups: group g's queue [qh, qt), kept in device memory when
+    // the loop leaves
+    long long qh = 0, qt = 0;
+    if (lane < kGroups) {
+        qh = (long long)ld_relaxed_gpu(reinterpret_cast<const unsigned long long *>(&a.mstate->qh[lane]));
+        qt = (long long)ld_relaxed_gpu(reinterpret_cast<const unsigned long long *>(&a.mstate->qt[lane]));
+    }
+    int cur = -1;
+    long long quota = 0;
+    for (;;) {
+        long long P = 0;
+        bool stop = false;
+        if (lane == 0) {
+            P = ld_acquire_sys(&a.ctrl->published);
+            stop = ld_relaxed_sys(&a.ctrl->stop) != 0;
+        }
+        P = __shfl_sync(FULL, P, 0);
+        if (__shfl_sync(FULL, (int)stop, 0)) break;
+        const bool arrived = P > from;
+        if (arrived) {
+            ld_acquire_sys(&a.ctrl->published);  // each lane orders its reads after the publication
+            for (long long q0 = from; q0 < P; q0 += 32) {
+                const int n = P - q0 < 32 ? (int)(P - q0) : 32;
+                for (int j = 0; j < n; j++) {
+                    const int64_t *src = reinterpret_cast<const int64_t *>(a.ring + ((q0 + j) & a.mask));
+                    int64_t *dst = reinterpret_cast<int64_t *>(a.dring + ((q0 + j) & a.mask));
+                    for (int i = lane; i < (int)(sizeof(SlotRec) / 8); i += 32) dst[i] = ld_relaxed_sys(src + i);
+                }
+                __threadfence();
+                __syncwarp();
+                // lane j takes request q0 + j
+                int gj = -1;
+                long long nt = 0;
+                if (lane < n) {
+                    const long long qq = q0 + lane, slot = qq & a.mask;
+                    const SlotRec *rec = a.dring + slot;
+                    nt = (long long)ld_relaxed_gpu(reinterpret_cast<const unsigned long long *>(&rec->ntiles));
+                    a.done[slot] = 0;
+                    a.sreq[slot] = qq;
+                    if (nt == 0) {
+                        complete_request(a, qq);  // nothing to move: complete at once
+                    } else {
+                        int kind, wsel;
+                        asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(kind) : "l"(&rec->kind) : "memory");
+                        asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(wsel) : "l"(&rec->op.wsel) : "memory");
+                        gj = group_of(kind, wsel);
+                    }
+                }
+                // queue them in admission order, each by its group's lane
+                for (int j = 0; j < n; j++) {
+                    const int gjj = __shfl_sync(FULL, gj, j);
+                    const long long ntj = __shfl_sync(FULL, nt, j);
+                    if (gjj >= 0 && lane == gjj) {
+                        a.gq[(long long)gjj * a.slots + (qt & a.mask)] = QEnt{q0 + j, ntj};
+                        qt++;
+                    }
+                }
+            }
+            from = P;
+            __threadfence();
+            __syncwarp();
+        }
+        // append while the unclaimed backlog is short
+        long long G = 0;
+        if (lane == 0) G = (long long)ld_relaxed_gpu(&a.claim->next);
+        long long backlog = tt - __shfl_sync(FULL, G, 0);
+        const long long ap0 = ap;
+        for (;;) {
+            const unsigned ne = __ballot_sync(FULL, lane < kGroups && qt > qh);
+            if (!ne || backlog >= a.backlog_target) break;
+            if (cur < 0 || !((ne >> cur) & 1u) || quota <= 0) {
+                // the group whose queued request is oldest
+                long long front = LLONG_MAX;
+                if ((ne >> lane) & 1u) front = a.gq[(long long)lane * a.slots + (qh & a.mask)].req;
+                long long best = front;
+                for (int o = 16; o > 0; o >>= 1) {
+                    const long long other = __shfl_xor_sync(FULL, best, o);
+                    best = other < best ? other : best;
+                }
+                cur = __ffs(__ballot_sync(FULL, front == best)) - 1;
+                quota = a.backlog_target;
+            }
+            // the entry this append rewrites must belong to a completed request
+            int ok = 1;
+            if (lane == 0 && ap >= a.slots) {
+                const long long old = a.alist[ap & a.mask].req;
+                const long long os = old & a.mask;
+                const long long occ = (long long)ld_relaxed_gpu(reinterpret_cast<const unsigned long long *>(&a.sreq[os]));
+                if (occ == old) {
+                    const long long dn = (long long)ld_relaxed_gpu(&a.done[os]);
+                    const long long ont = (long long)ld_relaxed_gpu(
+                        reinterpret_cast<const unsigned long long *>(&a.dring[os].ntiles));
+                    ok = dn == ont;
+                }
+            }
+            if (!__shfl_sync(FULL, ok, 0)) break;  // try again at the next poll
+            long long r = 0, nt = 0;
+            if (lane == cur) {
+                const QEnt e = a.gq[(long long)cur * a.slots + (qh & a.mask)];
+                r = e.req;
+                nt = e.nt;
+                qh++;
+            }
+            r = __shfl_sync(FULL, r, cur);
+            nt = __shfl_sync(FULL, nt, cur);
+            if (lane == 0) {
+                AppendEnt *e = a.alist + (ap & a.mask);
+                e->tag = ap;
+                e->req = r;
+                asm volatile("st.release.gpu.global.s64 [%0], %1;" ::"l"(&e->first), "l"(tt) : "memory");
+            }
+            tt += nt;
+            ap++;
+            backlog += nt;
+            quota -= nt;
+        }
+        if (ap > ap0) {
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) {
+                // apub before total: a warp that acquires the new total finds
+                // every request its tiles belong to
+                atomicExch(&a.pub->apub, (unsigned long long)ap);
+                __threadfence();
+                atomicExch(&a.pub->total, (unsigned long long)tt);
+            }
+        }
+        if (arrived && lane == 0) atomicExch(&a.pub->mirrored, (unsigned long long)from);
+        __syncwarp();
+        if (arrived || ap > ap0) {
+            idle_ns = 0;
+            backoff = 128;
+            continue;
+        }
+        // no progress: nothing arrived and nothing could be appended (the
+        // backlog is long enough, or an entry's request has not completed)
+        const bool queued = __ballot_sync(FULL, lane < kGroups && qt > qh) != 0;
+        idle_ns += queued ? 256 : backoff;
+        if (idle_ns > a.idle_budget_ns) {
+            // bounded: keep the queues for the next launch and leave; the
+            // other warps leave once they run out of tiles, and the host
+            // relaunches the loop while requests are outstanding (a request
+            // can wait on tiles that a warp claimed past the total and carried
+            // out of this launch)
+            if (lane < kGroups) {
+                a.mstate->qh[lane] = qh;
+                a.mstate->qt[lane] = qt;
+            }
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) atomicExch(&a.pub->mirror_gone, 1);
+            break;
+        }
+        if (queued) {
+            __nanosleep(256);
+        } else {
+            __nanosleep(backoff);
+            backoff = backoff < 2048 ? backoff * 2 : 2048;
+        }
+    }
+}
+
+// The mirroring warp (warp 0 of CTA 0) runs serve_mirror and nothing else:
+// it appends requests to the global tile sequence and publishes the new
+// total.  Every other warp claims ranges [next, next + k)
 // of that sequence with one fetch-add (which always succeeds: a
 // compare-and-swap claim fails whenever another claim lands between reading
 // the counter and swapping it, which at this claim rate is nearly always).  k
@@ -283,70 +498,12 @@ __global__ void __launch_bounds__(kThreads, kServeCtas) serve_kernel(ServeArgs a
     int64_t idle_ns = 0;
     unsigned backoff = 128;
     if (mirror) {
-        // this warp is the only writer of dpub and total: it reads them once
-        // (past L1) and keeps them in registers; a plain load could return a
-        // stale L1 copy of a word that the atomics below update in L2
-        long long from = (long long)ld_relaxed_gpu(&a.pub->dpub);
-        long long tt = (long long)ld_relaxed_gpu(&a.pub->total);
-        for (;;) {
-            long long P = 0;
-            bool stop = false;
-            if (lane == 0) {
-                P = ld_acquire_sys(&a.ctrl->published);
-                stop = ld_relaxed_sys(&a.ctrl->stop) != 0;
-            }
-            P = __shfl_sync(FULL, P, 0);
-            if (__shfl_sync(FULL, (int)stop, 0)) break;
-            if (P <= from) {
-                idle_ns += backoff;
-                if (idle_ns > a.idle_budget_ns) {
-                    // bounded: the host relaunches the loop on demand; the
-                    // other warps leave once they run out of tiles
-                    if (lane == 0) atomicExch(&a.pub->mirror_gone, 1);
-                    break;
-                }
-                __nanosleep(backoff);
-                backoff = backoff < 2048 ? backoff * 2 : 2048;
-                continue;
-            }
-            idle_ns = 0;
-            backoff = 128;
-            ld_acquire_sys(&a.ctrl->published);  // each lane orders its reads after the publication
-            for (long long qq = from; qq < P; qq++) {
-                const int64_t *src = reinterpret_cast<const int64_t *>(a.ring + (qq & a.mask));
-                int64_t *dst = reinterpret_cast<int64_t *>(a.dring + (qq & a.mask));
-                for (int i = lane; i < (int)(sizeof(SlotRec) / 8); i += 32) dst[i] = ld_relaxed_sys(src + i);
-            }
-            __threadfence();
-            __syncwarp();
-            if (lane == 0) {
-                for (long long qq = from; qq < P; qq++) {
-                    const long long slot = qq & a.mask;
-                    const long long nt = (long long)ld_relaxed_gpu(
-                        reinterpret_cast<const unsigned long long *>(&a.dring[slot].ntiles));
-                    a.done[slot] = 0;
-                    a.stile[slot].tag = qq;
-                    asm volatile("st.release.gpu.global.s64 [%0], %1;" ::"l"(&a.stile[slot].first), "l"(tt)
-                                 : "memory");
-                    if (nt == 0) complete_request(a, qq);  // nothing to move: complete at once
-                    tt += nt;
-                }
-                __threadfence();
-                // dpub before total: a warp that acquires the new total finds
-                // every request its tiles belong to
-                atomicExch(&a.pub->dpub, (unsigned long long)P);
-                __threadfence();
-                atomicExch(&a.pub->total, (unsigned long long)tt);
-            }
-            tt = __shfl_sync(FULL, tt, 0);
-            from = P;
-            __syncwarp();
-        }
+        serve_mirror(a, lane);
         return;
     }
     // lane 0's claim [cn, ce) and the request last found
     const int64_t gw = (int64_t)blockIdx.x * kWarps + w;
-    long long cn = 0, ce = 0, q = -1, qfirst = 0, qnt = 0;
+    long long cn = 0, ce = 0, q = -1, qr = -1, qfirst = 0, qnt = 0;
     if (lane == 0) {
         cn = a.held[gw].next;
         ce = a.held[gw].end;
@@ -428,11 +585,11 @@ __global__ void __launch_bounds__(kThreads, kServeCtas) serve_kernel(ServeArgs a
         // the request holding tile cn (lane 0's cached one, else a warp search)
         long long c = __shfl_sync(FULL, cn, 0);
         if (__shfl_sync(FULL, (int)(q < 0 || c < qfirst || c >= qfirst + qnt), 0)) {
-            // the total acquired before the claim bounds c; dpub was stored
+            // the total acquired before the claim bounds c; apub was stored
             // before that total, so every request holding tiles below it is
-            // among [.., dpub)
+            // among the positions [.., apub)
             long long dp = 0;
-            if (lane == 0) dp = (long long)ld_relaxed_gpu(&a.pub->dpub);
+            if (lane == 0) dp = (long long)ld_relaxed_gpu(&a.pub->apub);
             dp = __shfl_sync(FULL, dp, 0);
             long long lo = dp - a.slots > 0 ? dp - a.slots : 0;
             const long long qh = __shfl_sync(FULL, q, 0);
@@ -441,11 +598,13 @@ __global__ void __launch_bounds__(kThreads, kServeCtas) serve_kernel(ServeArgs a
             if (lane == 0) {
                 q = found;
                 if (q >= 0) {
-                    qfirst = (long long)ld_relaxed_gpu(
-                        reinterpret_cast<const unsigned long long *>(&a.stile[q & a.mask].first));
+                    const AppendEnt *e = a.alist + (q & a.mask);
+                    qfirst = (long long)ld_acquire_gpu(reinterpret_cast<const unsigned long long *>(&e->first));
+                    qr = (long long)ld_relaxed_gpu(reinterpret_cast<const unsigned long long *>(&e->req));
+                    const long long tg = (long long)ld_relaxed_gpu(reinterpret_cast<const unsigned long long *>(&e->tag));
                     qnt = (long long)ld_relaxed_gpu(
-                        reinterpret_cast<const unsigned long long *>(&a.dring[q & a.mask].ntiles));
-                    if (c < qfirst || c >= qfirst + qnt) q = -1;  // never expected: search again
+                        reinterpret_cast<const unsigned long long *>(&a.dring[qr & a.mask].ntiles));
+                    if (tg != q || c < qfirst || c >= qfirst + qnt) q = -1;  // never expected: search again
                 }
             }
             if (__shfl_sync(FULL, (int)(q < 0), 0)) {
@@ -460,7 +619,7 @@ __global__ void __launch_bounds__(kThreads, kServeCtas) serve_kernel(ServeArgs a
         }
         long long r = 0, t0 = 0, m = 0;
         if (lane == 0) {
-            r = q;
+            r = qr;
             t0 = cn - qfirst;
             m = (ce < qfirst + qnt ? ce : qfirst + qnt) - cn;
         }
@@ -543,14 +702,16 @@ namespace dte {
 // Largest claim a warp takes at once (tiles); the smallest is the loop's
 // span_tiles setting.
 constexpr int64_t kServeSpanMax = 64;
+// Largest span_tiles accepted.
+constexpr int64_t kServeSpanLimit = 1 << 16;
 
-// Layout of the device state: ClaimLine | PubLine | CqLine | SlotTile[slots] |
-// done[slots] | SlotRec[slots] | Held[warps].
+// Layout of the device state: ClaimLine | PubLine | CqLine | MirrorState | AppendEnt[slots] |
+// sreq[slots] | done[slots] | SlotRec[slots] | QEnt[kGroups * slots] | Held[warps].
 static size_t dstate_bytes(int64_t slots, int64_t warps)
 {
-    return sizeof(ClaimLine) + sizeof(PubLine) + sizeof(CqLine) +
-           (size_t)slots * (sizeof(SlotTile) + sizeof(unsigned long long) + sizeof(SlotRec)) +
-           (size_t)warps * sizeof(Held);
+    return sizeof(ClaimLine) + sizeof(PubLine) + sizeof(CqLine) + sizeof(MirrorState) +
+           (size_t)slots * (sizeof(AppendEnt) + sizeof(long long) + sizeof(unsigned long long) + sizeof(SlotRec)) +
+           (size_t)kGroups * (size_t)slots * sizeof(QEnt) + (size_t)warps * sizeof(Held);
 }
 
 static void server_launch(dte_server s)
@@ -563,12 +724,18 @@ static void server_launch(dte_server s)
     p += sizeof(PubLine);
     a.cq_tail = &reinterpret_cast<CqLine *>(p)->tail;
     p += sizeof(CqLine);
-    a.stile = reinterpret_cast<SlotTile *>(p);
-    p += (size_t)s->slots * sizeof(SlotTile);
+    a.mstate = reinterpret_cast<MirrorState *>(p);
+    p += sizeof(MirrorState);
+    a.alist = reinterpret_cast<AppendEnt *>(p);
+    p += (size_t)s->slots * sizeof(AppendEnt);
+    a.sreq = reinterpret_cast<long long *>(p);
+    p += (size_t)s->slots * sizeof(long long);
     a.done = reinterpret_cast<unsigned long long *>(p);
     p += (size_t)s->slots * sizeof(unsigned long long);
     a.dring = reinterpret_cast<SlotRec *>(p);
     p += (size_t)s->slots * sizeof(SlotRec);
+    a.gq = reinterpret_cast<QEnt *>(p);
+    p += (size_t)kGroups * (size_t)s->slots * sizeof(QEnt);
     a.held = reinterpret_cast<Held *>(p);
     a.ring = s->ring;
     a.ctrl = s->ctrl;
@@ -578,6 +745,8 @@ static void server_launch(dte_server s)
     a.span_min = s->span;
     a.span_max = std::max<int64_t>(s->span, kServeSpanMax);
     a.idle_budget_ns = s->idle_limit * 1000;
+    // enough unclaimed tiles for four claims of the smallest span per warp
+    a.backlog_target = 4 * ((int64_t)s->sms * s->ctas_per_sm * kWarps - 1) * a.span_min;
     __atomic_store_n(&s->ctrl->stop, (int64_t)0, __ATOMIC_RELEASE);
     // stream-ordered after the previous launch has ended
     if (cudaMemsetAsync(&a.pub->mirror_gone, 0, sizeof(int), s->stream) != cudaSuccess) {
@@ -668,7 +837,7 @@ int dte_server_create(const dte_server_config *cfg, dte_server *out)
     dte_server_config c{1024, (int64_t)8 << 30, 2, 8, 50000};
     if (cfg) c = *cfg;
     if (c.ring_slots <= 0 || (c.ring_slots & (c.ring_slots - 1)) || c.ring_slots > (1 << 20)) return DTE_ERR_ARG;
-    if (c.max_inflight_bytes <= 0 || c.ctas_per_sm < 1 || c.ctas_per_sm > kServeCtas || c.span_tiles < 1 ||
+    if (c.max_inflight_bytes <= 0 || c.ctas_per_sm < 1 || c.ctas_per_sm > kServeCtas || c.span_tiles < 1 || c.span_tiles > kServeSpanLimit ||
         c.idle_exit_us < 1)
         return DTE_ERR_ARG;
     int dev = 0;

@@ -141,6 +141,9 @@ def test_server_argument_errors():
     with pytest.raises(dte.DteError) as e:
         dte.dte_server_create(ring_slots=3)
     assert e.value.code == dte.ERR_ARG
+    with pytest.raises(dte.DteError) as e:
+        dte.dte_server_create(span_tiles=1 << 17)
+    assert e.value.code == dte.ERR_ARG
     srv = dte.dte_server_create()
     try:
         ov = dte.Datatype.vector(4, 3, 2, dte.FLOAT32).commit()
@@ -158,3 +161,39 @@ def test_server_argument_errors():
         dte.dte_server_wait(srv, tk, 2_000_000)
     finally:
         dte.dte_server_free(srv)
+
+
+def test_over_claims_carried_across_relaunches():
+    """Warps racing for a group's last tiles claim past its published end and
+    keep those positions for the group's next requests, across the loop's
+    exits and relaunches: small requests of one kernel variant with pauses
+    longer than the idle exit between them, claims of up to 64 tiles, then
+    the other direction and a burst of both."""
+    rng = np.random.default_rng(604)
+    spec = ("vector", 4096, 4, 8, ("basic", "float32"))  # 64 KiB packed: 64 tiles
+    t = dte.Datatype.from_spec(spec).commit()
+    o = oracle.from_spec(spec)
+    reqs = []
+    for i in range(24):
+        kind = dte.BATCH_PACK if i < 10 or (i >= 16 and i % 2) else dte.BATCH_UNPACK
+        span = t.true_lb + t.true_extent
+        reqs.append(dict(t=t, kind=kind, spec=spec, user=rng.integers(0, 256, span, dtype=np.uint8),
+                         packed=rng.integers(0, 256, t.size, dtype=np.uint8)))
+    assert o.size == t.size
+    ref = reference(reqs)
+    srv = dte.dte_server_create(idle_exit_us=1000, span_tiles=64)
+    try:
+        bufs = buffers(reqs)
+        tickets = []
+        for i, (r, (u, p)) in enumerate(zip(reqs, bufs)):
+            tickets.append(dte.dte_server_submit(srv, r["kind"], r["t"].h, 1, u.data_ptr(), p.data_ptr()))
+            if i < 16:
+                dte.dte_server_wait(srv, tickets[-1])
+                time.sleep(0.01)  # long enough for the loop to leave
+        for tk in tickets:
+            dte.dte_server_wait(srv, tk)
+        got = outputs(reqs, bufs)
+    finally:
+        dte.dte_server_free(srv)
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b)
