@@ -245,6 +245,10 @@ __device__ __forceinline__ void complete_request(const ServeArgs &a, long long r
 #define DTE_SERVE_CTAS 2
 #endif
 constexpr int kServeCtas = DTE_SERVE_CTAS;  // most CTAs per SM the loop is compiled for
+#ifndef DTE_SERVE_QUOTA
+#define DTE_SERVE_QUOTA 4
+#endif
+constexpr long long kServeQuota = DTE_SERVE_QUOTA;  // a group's run, in backlog targets
 
 // Requests wait in the mirroring warp's reorder stage in groups that share a
 // kernel variant: direction x word class.
@@ -365,7 +369,7 @@ __device__ __forceinline__ void serve_mirror(const ServeArgs &a, int lane)
                     best = other < best ? other : best;
                 }
                 cur = __ffs(__ballot_sync(FULL, front == best)) - 1;
-                quota = a.backlog_target;
+                quota = a.backlog_target * kServeQuota;
             }
             // the entry this append rewrites must belong to a completed request
             int ok = 1;
@@ -701,6 +705,12 @@ namespace dte {
 
 // Largest claim a warp takes at once (tiles); the smallest is the loop's
 // span_tiles setting.
+#ifndef DTE_SERVE_BACKLOG
+#define DTE_SERVE_BACKLOG 4
+#endif
+// Unclaimed tiles, in claims of span_tiles per claiming warp, above which the
+// mirroring warp holds requests back in its per-variant queues.
+constexpr int64_t kServeBacklog = DTE_SERVE_BACKLOG;
 constexpr int64_t kServeSpanMax = 64;
 // Largest span_tiles accepted.
 constexpr int64_t kServeSpanLimit = 1 << 16;
@@ -745,8 +755,8 @@ static void server_launch(dte_server s)
     a.span_min = s->span;
     a.span_max = std::max<int64_t>(s->span, kServeSpanMax);
     a.idle_budget_ns = s->idle_limit * 1000;
-    // enough unclaimed tiles for four claims of the smallest span per warp
-    a.backlog_target = 4 * ((int64_t)s->sms * s->ctas_per_sm * kWarps - 1) * a.span_min;
+    // enough unclaimed tiles for a few claims of the smallest span per warp
+    a.backlog_target = kServeBacklog * ((int64_t)s->sms * s->ctas_per_sm * kWarps - 1) * a.span_min;
     __atomic_store_n(&s->ctrl->stop, (int64_t)0, __ATOMIC_RELEASE);
     // stream-ordered after the previous launch has ended
     if (cudaMemsetAsync(&a.pub->mirror_gone, 0, sizeof(int), s->stream) != cudaSuccess) {
