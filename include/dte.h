@@ -457,10 +457,12 @@ DTE_API int dte_op_shape_query(const dte_op *op, dte_op_shape *out);
 DTE_API int dte_pack_batch_enqueue_noalloc(int64_t nops, const dte_op *ops, dte_stream_t stream);
 
 /* Number of bounded device waits that gave up on the current device since
- * the library was loaded (the bulk-copy kernels wait on shared-memory
+ * the library was loaded.  The bulk-copy kernels wait on shared-memory
  * barriers with a time budget of about a second; a wait that runs out is
  * counted here and the kernel drains what it issued and returns instead of
- * hanging).  Synchronises with the device.  Expected to stay 0. */
+ * hanging.  A request-loop warp whose tile search keeps finding nothing for
+ * the loop's idle budget is counted too (it keeps its claim for the next
+ * launch and leaves).  Synchronises with the device.  Expected to stay 0. */
 DTE_API int dte_device_timeouts(int64_t *count);
 
 /* ------------------------------------------------------------------------

@@ -147,4 +147,6 @@ int device_blob_resident(dte_type t, int dev, const char **out);
 void note_use(dte_type t, int device, void *stream);
 // Free device copies whose pending work has finished.
 void reap_deferred();
+// Request-loop waits that gave up on the current device (server.cu).
+int serve_timeouts(unsigned long long *v);
 }  // namespace dte

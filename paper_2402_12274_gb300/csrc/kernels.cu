@@ -1467,15 +1467,17 @@ extern "C" int dte_pack_adjoint_f32_enqueue(const void *gy, int64_t count, dte_t
     }
 }
 
-// Bounded device waits that gave up (bulk kernels), on the current device.
+// Bounded device waits that gave up (bulk kernels and the request loop), on
+// the current device.
 extern "C" int dte_device_timeouts(int64_t *count)
 {
     if (!count) return DTE_ERR_ARG;
-    unsigned long long v = 0;
+    unsigned long long v = 0, sv = 0;
     if (cudaMemcpyFromSymbol(&v, dte::g_bulk_timeouts, sizeof v) != cudaSuccess) {
         cudaGetLastError();
         return DTE_ERR_CUDA;
     }
-    *count = (int64_t)v;
+    if (int rc = dte::serve_timeouts(&sv)) return rc;
+    *count = (int64_t)(v + sv);
     return DTE_SUCCESS;
 }

@@ -241,6 +241,10 @@ __device__ __forceinline__ void complete_request(const ServeArgs &a, long long r
     st_release_sys(a.cq + (long long)(pos & (unsigned long long)a.mask), r + 1);
 }
 
+// Request-loop waits that gave up (a tile search that kept finding nothing),
+// on this device; read by dte_device_timeouts.
+__device__ unsigned long long g_serve_timeouts;
+
 #ifndef DTE_SERVE_CTAS
 #define DTE_SERVE_CTAS 2
 #endif
@@ -514,6 +518,7 @@ __global__ void __launch_bounds__(kThreads, kServeCtas) serve_kernel(ServeArgs a
         a.held[gw] = Held{0, 0};
     }
     int64_t cached = -1;  // request whose record is in wop[w]
+    int64_t miss_ns = 0;  // time spent retrying a tile search that found nothing
     Hint h{-1, 0};        // search position in that request's descriptor
     unsigned ep = 0;  // lane 0: the CTA's epoch before its last look at the total
     for (;;) {
@@ -612,14 +617,23 @@ __global__ void __launch_bounds__(kThreads, kServeCtas) serve_kernel(ServeArgs a
                 }
             }
             if (__shfl_sync(FULL, (int)(q < 0), 0)) {
-                // bounded like an idle poll; a loop that gives up leaves the
-                // claim's request incomplete, which the host's bounded wait
-                // reports as a timeout
-                idle_ns += 256;
-                if (idle_ns > a.idle_budget_ns) break;
+                // never expected; retried under a budget of its own (the idle
+                // budget's length).  On expiry the warp counts a device
+                // timeout (dte_device_timeouts), keeps its claim for the next
+                // launch and leaves; the claim's request stays incomplete
+                // until then, which the host's bounded wait reports
+                miss_ns += 256;
+                if (miss_ns > a.idle_budget_ns) {
+                    if (lane == 0) {
+                        atomicAdd(&g_serve_timeouts, 1ull);
+                        a.held[gw] = Held{cn, ce};
+                    }
+                    break;
+                }
                 __nanosleep(256);
                 continue;
             }
+            miss_ns = 0;
         }
         long long r = 0, t0 = 0, m = 0;
         if (lane == 0) {
@@ -825,6 +839,16 @@ static int server_progress(dte_server s)
                 if (!s->launched) return DTE_ERR_CUDA;
             }
         }
+    }
+    return DTE_SUCCESS;
+}
+
+// Request-loop waits that gave up on the current device (see g_serve_timeouts).
+int serve_timeouts(unsigned long long *v)
+{
+    if (cudaMemcpyFromSymbol(v, g_serve_timeouts, sizeof *v) != cudaSuccess) {
+        cudaGetLastError();
+        return DTE_ERR_CUDA;
     }
     return DTE_SUCCESS;
 }

@@ -95,6 +95,7 @@ def test_results_identical_alone_and_in_the_mix():
     for a, b, c in zip(ref, alone, mixed):
         assert np.array_equal(a, b)
         assert np.array_equal(a, c)
+    assert dte.dte_device_timeouts() == 0
 
 
 def test_admission_under_a_small_byte_cap():
