@@ -398,7 +398,10 @@ enum dte_plan {
 
 /* Set the plan of a type handle (any DTE_PLAN_*; DTE_ERR_ARG otherwise;
  * DTE_ERR_TYPE for a predefined handle).  Affects moves enqueued and
- * batches created afterwards; dte_type_dup copies it. */
+ * batches created afterwards; dte_type_dup copies it.  A type starts with
+ * DTE_PLAN_AUTO, or with the plan named by the environment variable
+ * DTE_PLAN (auto, chunk, chunk_wide, segment or bulk; read once per process)
+ * when it is committed with DTE_PLAN_AUTO still set. */
 DTE_API int dte_type_set_plan(dte_type type, int plan);
 DTE_API int dte_type_get_plan(dte_type type, int *plan);
 
@@ -485,7 +488,9 @@ typedef struct dte_server_s *dte_server;
 typedef struct dte_server_config {
     int64_t ring_slots;          /* requests admitted at once; power of two <= 2^20 (default 1024) */
     int64_t max_inflight_bytes;  /* cap on moved bytes (2*count*size) of admitted, unfinished
-                                    requests (default 8 GiB); a larger request is admitted alone */
+                                    requests; a larger request is admitted alone.  0 = the
+                                    default: DTE_SERVE_MAX_INFLIGHT_BYTES from the environment
+                                    (a positive integer) if set, else 8 GiB */
     int32_t ctas_per_sm;         /* persistent CTAs per SM, 1 or 2 (default 2) */
     int32_t span_tiles;          /* fewest tiles (1-2 KiB, or 32-segment rounds) a warp claims at once,
                                     1..65536; claims grow to 64 while many published tiles are

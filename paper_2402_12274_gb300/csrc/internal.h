@@ -150,3 +150,17 @@ void reap_deferred();
 // Request-loop waits that gave up on the current device (server.cu).
 int serve_timeouts(unsigned long long *v);
 }  // namespace dte
+
+#include <nvtx3/nvToolsExt.h>
+namespace dte {
+// An NVTX range over one ABI call, named after it, for Nsight timelines.
+// Without a tool attached, the push and the pop each test one function
+// pointer.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace dte
+#define DTE_NVTX_RANGE(name) ::dte::NvtxRange dte_nvtx_range_(name)

@@ -657,6 +657,7 @@ extern "C" {
 int dte_pack_enqueue(const void *inbuf, int64_t incount, dte_type type, void *outbuf, int64_t outsize,
                      int64_t *position, dte_stream_t stream)
 {
+    DTE_NVTX_RANGE("dte_pack_enqueue");
     try {
         if (!handle_valid(type)) return DTE_ERR_TYPE;
         if (!type->committed) return DTE_ERR_TYPE;
@@ -686,6 +687,7 @@ int dte_pack_enqueue(const void *inbuf, int64_t incount, dte_type type, void *ou
 int dte_unpack_enqueue(const void *inbuf, int64_t insize, int64_t *position, void *outbuf, int64_t outcount,
                        dte_type type, dte_stream_t stream)
 {
+    DTE_NVTX_RANGE("dte_unpack_enqueue");
     try {
         if (!handle_valid(type)) return DTE_ERR_TYPE;
         if (!type->committed) return DTE_ERR_TYPE;
@@ -716,6 +718,7 @@ int dte_unpack_enqueue(const void *inbuf, int64_t insize, int64_t *position, voi
 int dte_pack_range_enqueue(const void *inbuf, int64_t incount, dte_type type, int64_t first, int64_t nbytes,
                            void *outbuf, dte_stream_t stream)
 {
+    DTE_NVTX_RANGE("dte_pack_range_enqueue");
     try {
         if (!handle_valid(type)) return DTE_ERR_TYPE;
         if (!type->committed) return DTE_ERR_TYPE;
@@ -742,6 +745,7 @@ int dte_pack_range_enqueue(const void *inbuf, int64_t incount, dte_type type, in
 int dte_unpack_range_enqueue(const void *inbuf, int64_t first, int64_t nbytes, void *outbuf, int64_t outcount,
                              dte_type type, dte_stream_t stream)
 {
+    DTE_NVTX_RANGE("dte_unpack_range_enqueue");
     try {
         if (!handle_valid(type)) return DTE_ERR_TYPE;
         if (!type->committed) return DTE_ERR_TYPE;
@@ -777,6 +781,7 @@ int dte_sendrecv_enqueue(const void *sendbuf, int64_t sendcount, dte_type sendty
                          int64_t recvcount, dte_type recvtype, void *staging, int64_t staging_bytes,
                          dte_stream_t stream)
 {
+    DTE_NVTX_RANGE("dte_sendrecv_enqueue");
     try {
         if (!handle_valid(sendtype) || !handle_valid(recvtype)) return DTE_ERR_TYPE;
         if (!sendtype->committed || !recvtype->committed) return DTE_ERR_TYPE;
@@ -964,6 +969,7 @@ int dte_batch_set_launch(dte_batch batch, int blocks_per_sm, int64_t span_tiles)
 
 int dte_batch_enqueue(dte_batch b, dte_stream_t stream)
 {
+    DTE_NVTX_RANGE("dte_batch_enqueue");
     if (!batch_valid(b)) return DTE_ERR_ARG;
     if (b->ntiles == 0) return DTE_SUCCESS;
     int dev = -1;
@@ -1042,6 +1048,7 @@ int dte_unpack_batch_enqueue(int64_t nops, const dte_op *ops, dte_stream_t strea
 int dte_type_iov_async(dte_type type, int64_t count, int64_t iov_offset, dte_iov *d_iov, int64_t max_iov_len,
                        int64_t *d_actual_iov_len, const void *base, dte_stream_t stream)
 {
+    DTE_NVTX_RANGE("dte_type_iov_async");
     try {
         if (!handle_valid(type)) return DTE_ERR_TYPE;
         if (!type->committed) return DTE_ERR_TYPE;
@@ -1091,6 +1098,7 @@ int dte_type_iov_async(dte_type type, int64_t count, int64_t iov_offset, dte_iov
 int dte_type_iov_len_async(dte_type type, int64_t n, const int64_t *d_budget, int64_t *d_iov_len,
                            int64_t *d_iov_bytes, dte_stream_t stream)
 {
+    DTE_NVTX_RANGE("dte_type_iov_len_async");
     try {
         if (!handle_valid(type)) return DTE_ERR_TYPE;
         if (!type->committed) return DTE_ERR_TYPE;
@@ -1119,6 +1127,7 @@ int dte_type_iov_at_bytes_async(dte_type type, int64_t n, const int64_t *d_offse
                                 dte_iov *d_iov, int64_t *d_first, int64_t *d_actual, const void *base,
                                 dte_stream_t stream)
 {
+    DTE_NVTX_RANGE("dte_type_iov_at_bytes_async");
     try {
         if (!handle_valid(type)) return DTE_ERR_TYPE;
         if (!type->committed) return DTE_ERR_TYPE;
@@ -1256,6 +1265,7 @@ static int noalloc_scratch(int dev, char **out)
 
 extern "C" int dte_pack_batch_enqueue_noalloc(int64_t nops, const dte_op *ops, dte_stream_t stream)
 {
+    DTE_NVTX_RANGE("dte_pack_batch_enqueue_noalloc");
     try {
         if (nops < 0 || (nops > 0 && !ops)) return DTE_ERR_ARG;
         if (nops > kNoAllocMaxOps) return DTE_ERR_UNSUPPORTED;
@@ -1416,6 +1426,7 @@ static int adjoint_inverse(dte_type t, int64_t count, int dev, AdjointInverse *o
 extern "C" int dte_pack_adjoint_f32_enqueue(const void *gy, int64_t count, dte_type type, void *gx,
                                             dte_stream_t stream)
 {
+    DTE_NVTX_RANGE("dte_pack_adjoint_f32_enqueue");
     try {
         if (!handle_valid(type)) return DTE_ERR_TYPE;
         if (!type->committed) return DTE_ERR_TYPE;

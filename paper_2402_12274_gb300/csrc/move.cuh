@@ -461,6 +461,11 @@ __device__ __forceinline__ void shared_list_round(const Op &op, const DNode *nod
 // the warp decode of shared-child root lists (the batch kernels leave it out:
 // under their 64-register budget the extra path costs the common layouts
 // more than it gives the rare index-of-struct ones).
+#ifndef DTE_SEG_RUNU
+#define DTE_SEG_RUNU 4
+#endif
+constexpr int kSegRunU = DTE_SEG_RUNU;  // words in flight per lane in a round's run-by-run copy
+
 template <int W, bool PACK, bool LISTDEC = true>
 __device__ __forceinline__ void seg_round(const Op &op, const DNode *nodes, const char *blob, int64_t nseg_elem,
                                           const FastDiv &div_nseg, int64_t base, int64_t s1, int lane, Hint &h,
@@ -499,13 +504,13 @@ __device__ __forceinline__ void seg_round(const Op &op, const DNode *nodes, cons
             const char *src = PACK ? op.user_in + disp + (a - ps) : op.packed_in - op.pbase + a;
             char *dst = PACK ? op.packed_out - op.pbase + a : op.user_out + disp + (a - ps);
             const int n = (int)(e - a);
-            for (int o = 0; o < n; o += 4 * W) {
-                T v[4];
+            for (int o = 0; o < n; o += kSegRunU * W) {
+                T v[kSegRunU];
 #pragma unroll
-                for (int u = 0; u < 4; u++)
+                for (int u = 0; u < kSegRunU; u++)
                     if (o + u * W < n) v[u] = ldw<W>(src + o + u * W);
 #pragma unroll
-                for (int u = 0; u < 4; u++)
+                for (int u = 0; u < kSegRunU; u++)
                     if (o + u * W < n) stw<W>(dst + o + u * W, v[u]);
             }
         }

@@ -33,6 +33,7 @@
 #include <atomic>
 #include <chrono>
 #include <climits>
+#include <cstdlib>
 #include <deque>
 #include <vector>
 
@@ -853,6 +854,18 @@ int serve_timeouts(unsigned long long *v)
     return DTE_SUCCESS;
 }
 
+// The byte cap of a loop created without one: DTE_SERVE_MAX_INFLIGHT_BYTES
+// (a positive integer) if set, else 8 GiB.
+static int64_t default_cap()
+{
+    if (const char *v = std::getenv("DTE_SERVE_MAX_INFLIGHT_BYTES")) {
+        char *end = nullptr;
+        const long long x = std::strtoll(v, &end, 10);
+        if (end != v && *end == '\0' && x > 0) return (int64_t)x;
+    }
+    return (int64_t)8 << 30;
+}
+
 static bool ticket_done(dte_server s, int64_t ticket)
 {
     if (ticket >= s->next_req) return false;  // still queued on the host
@@ -868,8 +881,9 @@ extern "C" {
 int dte_server_create(const dte_server_config *cfg, dte_server *out)
 {
     if (!out) return DTE_ERR_ARG;
-    dte_server_config c{1024, (int64_t)8 << 30, 2, 8, 50000};
+    dte_server_config c{1024, 0, 2, 8, 50000};
     if (cfg) c = *cfg;
+    if (c.max_inflight_bytes == 0) c.max_inflight_bytes = default_cap();
     if (c.ring_slots <= 0 || (c.ring_slots & (c.ring_slots - 1)) || c.ring_slots > (1 << 20)) return DTE_ERR_ARG;
     if (c.max_inflight_bytes <= 0 || c.ctas_per_sm < 1 || c.ctas_per_sm > kServeCtas || c.span_tiles < 1 || c.span_tiles > kServeSpanLimit ||
         c.idle_exit_us < 1)
@@ -914,6 +928,7 @@ int dte_server_create(const dte_server_config *cfg, dte_server *out)
 
 int dte_server_submit(dte_server s, int kind, const dte_op *op, int64_t *ticket)
 {
+    DTE_NVTX_RANGE("dte_server_submit");
     try {
         if (!s || !op || !ticket) return DTE_ERR_ARG;
         if (kind != DTE_BATCH_PACK && kind != DTE_BATCH_UNPACK) return DTE_ERR_ARG;

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <unordered_map>
 #include <unordered_set>
@@ -1108,6 +1109,28 @@ int dte_type_dup(dte_type old, dte_type *out)
     DTE_CATCH
 }
 
+}  // extern "C"
+
+namespace dte {
+// The kernel plan that DTE_PLAN (auto, chunk, chunk_wide, segment or bulk)
+// gives every type at commit, or -1 when it is unset or names no plan; read
+// once per process.
+static int env_plan()
+{
+    static const int plan = [] {
+        const char *v = std::getenv("DTE_PLAN");
+        if (!v) return -1;
+        static const char *const names[] = {"auto", "chunk", "chunk_wide", "segment", "bulk"};
+        for (int i = 0; i < 5; i++)
+            if (std::strcmp(v, names[i]) == 0) return i;
+        return -1;
+    }();
+    return plan;
+}
+}  // namespace dte
+
+extern "C" {
+
 int dte_type_commit(dte_type *type)
 {
     DTE_TRY
@@ -1118,6 +1141,7 @@ int dte_type_commit(dte_type *type)
     if (t->committed) return DTE_SUCCESS;
     t->desc = commit_node(t->node);
     t->committed = true;
+    if (t->plan == DTE_PLAN_AUTO && env_plan() > 0) t->plan = env_plan();
     if (have_device()) {
         const char *p;
         int dev;

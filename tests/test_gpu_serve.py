@@ -198,3 +198,25 @@ def test_over_claims_carried_across_relaunches():
         dte.dte_server_free(srv)
     for a, b in zip(ref, got):
         assert np.array_equal(a, b)
+
+
+def test_default_cap_from_the_environment(monkeypatch):
+    """A loop created without a byte cap takes DTE_SERVE_MAX_INFLIGHT_BYTES."""
+    monkeypatch.setenv("DTE_SERVE_MAX_INFLIGHT_BYTES", str(96 << 10))
+    rng = np.random.default_rng(605)
+    reqs = make_requests(rng, 30, lo=16 << 10, hi=64 << 10)
+    ref = reference(reqs)
+    srv = dte.dte_server_create(ring_slots=64)  # max_inflight_bytes 0: the default
+    try:
+        bufs = buffers(reqs)
+        tickets = [dte.dte_server_submit(srv, r["kind"], r["t"].h, 1, u.data_ptr(), p.data_ptr())
+                   for r, (u, p) in zip(reqs, bufs)]
+        inflight, queued = dte.dte_server_progress(srv)
+        assert queued > 0  # 96 KiB held most requests back on the host
+        for tk in tickets:
+            dte.dte_server_wait(srv, tk)
+        got = outputs(reqs, bufs)
+    finally:
+        dte.dte_server_free(srv)
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b)
