@@ -220,3 +220,28 @@ def test_default_cap_from_the_environment(monkeypatch):
         dte.dte_server_free(srv)
     for a, b in zip(ref, got):
         assert np.array_equal(a, b)
+
+
+def test_reorder_stage_under_a_backlog():
+    """With span_tiles 1 the reorder stage holds requests back once about
+    four tiles per warp are unclaimed: a burst of mixed-variant requests then
+    runs through its per-variant queues.  A 16-slot ring makes the append
+    positions wrap many times, so entries are reused only after their
+    requests completed.  Every result must match the oracle."""
+    rng = np.random.default_rng(606)
+    reqs = make_requests(rng, 120, lo=256 << 10, hi=2 << 20)
+    ref = reference(reqs)
+    srv = dte.dte_server_create(ring_slots=16, span_tiles=1, max_inflight_bytes=1 << 40)
+    try:
+        bufs = buffers(reqs)
+        tickets = [dte.dte_server_submit(srv, r["kind"], r["t"].h, 1, u.data_ptr(), p.data_ptr())
+                   for r, (u, p) in zip(reqs, bufs)]
+        for tk in tickets:
+            dte.dte_server_wait(srv, tk)
+        assert dte.dte_server_progress(srv) == (0, 0)
+        got = outputs(reqs, bufs)
+    finally:
+        dte.dte_server_free(srv)
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b)
+    assert dte.dte_device_timeouts() == 0
