@@ -106,7 +106,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) seg_kernel(Desc d, Op op
     for (int64_t s0 = warp * span; s0 < nsegs; s0 += stride) {
         const int64_t s1 = min(s0 + span, nsegs);
         for (int64_t base = s0; base < s1; base += 32)
-            seg_round<W, PACK>(op, nodes, blob, nseg_elem, div_nseg, seg0 + base, seg0 + s1, lane, h, rh);
+            seg_round<W, PACK, true, kSegWide>(op, nodes, blob, nseg_elem, div_nseg, seg0 + base, seg0 + s1, lane, h,
+                                               rh);
     }
 }
 

@@ -456,17 +456,27 @@ __device__ __forceinline__ void shared_list_round(const Op &op, const DNode *nod
     }
 }
 
-// One round: segments [base, base + 32) clipped to s1 (warp-uniform args).
-// `rh` is the warp's search position in a root index list.  LISTDEC enables
-// the warp decode of shared-child root lists (the batch kernels leave it out:
-// under their 64-register budget the extra path costs the common layouts
-// more than it gives the rare index-of-struct ones).
 #ifndef DTE_SEG_RUNU
 #define DTE_SEG_RUNU 4
 #endif
 constexpr int kSegRunU = DTE_SEG_RUNU;  // words in flight per lane in a round's run-by-run copy
+#ifndef DTE_SEG_WIDE
+#define DTE_SEG_WIDE 16
+#endif
+// Widest user-side access (8 or 16 bytes; 0 = none) the single-move
+// segment-major kernel's run-by-run copy of 4-byte words takes where the
+// user side is aligned for it.
+constexpr int kSegWide = DTE_SEG_WIDE;
 
-template <int W, bool PACK, bool LISTDEC = true>
+// One round: segments [base, base + 32) clipped to s1 (warp-uniform args).
+// `rh` is the warp's search position in a root index list.  LISTDEC enables
+// the warp decode of shared-child root lists (the batch kernels leave it out:
+// under their 64-register budget the extra path costs the common layouts
+// more than it gives the rare index-of-struct ones).  WIDEUSER (8 or 16)
+// lets the run-by-run copy of 4-byte words take user-side accesses that wide
+// where the user side is aligned (the batch kernels leave it at 0: their
+// short runs of 2- and 4-byte elements got slower with it).
+template <int W, bool PACK, bool LISTDEC = true, int WIDEUSER = 0>
 __device__ __forceinline__ void seg_round(const Op &op, const DNode *nodes, const char *blob, int64_t nseg_elem,
                                           const FastDiv &div_nseg, int64_t base, int64_t s1, int lane, Hint &h,
                                           Hint &rh)
@@ -504,14 +514,66 @@ __device__ __forceinline__ void seg_round(const Op &op, const DNode *nodes, cons
             const char *src = PACK ? op.user_in + disp + (a - ps) : op.packed_in - op.pbase + a;
             char *dst = PACK ? op.packed_out - op.pbase + a : op.user_out + disp + (a - ps);
             const int n = (int)(e - a);
-            for (int o = 0; o < n; o += kSegRunU * W) {
-                T v[kSegRunU];
+            const uintptr_t ua = (uintptr_t)(PACK ? src : dst);
+            if (WIDEUSER >= 8 && W == 4 && (ua & 7) == 0) {
+                // the user side takes wider accesses: 16 bytes where it is
+                // 16-byte aligned, else 8, then one more pair and a last
+                // word; the packed side keeps 4-byte words
+                int o = 0;
+                if (WIDEUSER >= 16 && (ua & 15) == 0) {
+                    for (; o + 16 <= n; o += 16) {
+                        if (PACK) {
+                            const uint4 x = ldw<16>(src + o);
+                            stw<4>(dst + o, x.x);
+                            stw<4>(dst + o + 4, x.y);
+                            stw<4>(dst + o + 8, x.z);
+                            stw<4>(dst + o + 12, x.w);
+                        } else {
+                            uint4 x;
+                            x.x = ldw<4>(src + o);
+                            x.y = ldw<4>(src + o + 4);
+                            x.z = ldw<4>(src + o + 8);
+                            x.w = ldw<4>(src + o + 12);
+                            stw<16>(dst + o, x);
+                        }
+                    }
+                }
+                for (; o + 16 <= n; o += 16) {
+                    if (PACK) {
+                        const unsigned long long x = ldw<8>(src + o), y = ldw<8>(src + o + 8);
+                        stw<4>(dst + o, (uint32_t)x);
+                        stw<4>(dst + o + 4, (uint32_t)(x >> 32));
+                        stw<4>(dst + o + 8, (uint32_t)y);
+                        stw<4>(dst + o + 12, (uint32_t)(y >> 32));
+                    } else {
+                        const uint32_t x0 = ldw<4>(src + o), x1 = ldw<4>(src + o + 4);
+                        const uint32_t y0 = ldw<4>(src + o + 8), y1 = ldw<4>(src + o + 12);
+                        stw<8>(dst + o, (unsigned long long)x1 << 32 | x0);
+                        stw<8>(dst + o + 8, (unsigned long long)y1 << 32 | y0);
+                    }
+                }
+                if (o + 8 <= n) {
+                    if (PACK) {
+                        const unsigned long long x = ldw<8>(src + o);
+                        stw<4>(dst + o, (uint32_t)x);
+                        stw<4>(dst + o + 4, (uint32_t)(x >> 32));
+                    } else {
+                        const uint32_t x0 = ldw<4>(src + o), x1 = ldw<4>(src + o + 4);
+                        stw<8>(dst + o, (unsigned long long)x1 << 32 | x0);
+                    }
+                    o += 8;
+                }
+                if (o < n) stw<4>(dst + o, ldw<4>(src + o));  // lengths are multiples of W
+            } else {
+                for (int o = 0; o < n; o += kSegRunU * W) {
+                    T v[kSegRunU];
 #pragma unroll
-                for (int u = 0; u < kSegRunU; u++)
-                    if (o + u * W < n) v[u] = ldw<W>(src + o + u * W);
+                    for (int u = 0; u < kSegRunU; u++)
+                        if (o + u * W < n) v[u] = ldw<W>(src + o + u * W);
 #pragma unroll
-                for (int u = 0; u < kSegRunU; u++)
-                    if (o + u * W < n) stw<W>(dst + o + u * W, v[u]);
+                    for (int u = 0; u < kSegRunU; u++)
+                        if (o + u * W < n) stw<W>(dst + o + u * W, v[u]);
+                }
             }
         }
         return;
