@@ -195,6 +195,53 @@ def record_indexed_spec(rng: np.random.Generator, nblocks: int, mean_len: float 
     return ("indexed", bl, disp.astype(np.int64), rec)
 
 
+def record_variety_spec(rng: np.random.Generator, nblocks: int):
+    """An array of records under an index list, with the record drawn at
+    random.  A grain g of 1, 2, 4 or 8 bytes is drawn first; the record is a
+    struct of 1-6 blocks (1-5 elements each) of basic types at least g bytes
+    wide, at increasing displacements 0-12 bytes apart in multiples of g, or a
+    single block of one such type, and is resized with probability 0.7 to its
+    extent plus 0-12 bytes (a multiple of g).  It sits inside an indexed type
+    (displacements in records, sorted, Geometric(mean) block lengths with mean
+    1, 3 or 8 and Geometric(1/2) gaps on {0,1,...}) or a hindexed type (the
+    same displacements in bytes, shifted by a multiple of g in [-64, 64])."""
+    sizes = {"byte": 1, "int16": 2, "bfloat16": 2, "int32": 4, "float32": 4, "float64": 8}
+    g = int(rng.choice([1, 2, 4, 8]))
+    names = [n for n, z in sizes.items() if z >= g]
+
+    def pad():
+        return g * int(rng.integers(0, 12 // g + 1))
+
+    if rng.random() < 0.2:
+        el = str(rng.choice(names))
+        rec = ("contig", int(rng.integers(1, 9)), ("basic", el))
+        span = sizes[el] * rec[1]
+    else:
+        nb = int(rng.integers(1, 7))
+        kids = [("basic", str(rng.choice(names))) for _ in range(nb)]
+        bl = rng.integers(1, 6, nb).astype(np.int64)
+        d, at = [], 0
+        for kid, b in zip(kids, bl):
+            s = sizes[kid[1]]
+            at = -(-at // s) * s  # natural alignment of the block's element
+            d.append(at)
+            at += int(b) * s + pad()
+        rec = ("struct", bl, np.array(d, np.int64), kids)
+        span = at
+    if rng.random() < 0.7:
+        rec = ("resized", 0, span + pad(), rec)
+    mean = float(rng.choice([1.0, 3.0, 8.0]))
+    lens = rng.geometric(1.0 / mean, nblocks).astype(np.int64)
+    gaps = (rng.geometric(0.5, nblocks) - 1).astype(np.int64)
+    disp = np.cumsum(gaps + lens) - lens
+    disp -= disp[0]
+    if rng.random() < 0.5:
+        return ("indexed", lens, disp.astype(np.int64), rec)
+    ext = span + 16  # byte displacements: records at least this far apart
+    shift = g * int(rng.integers(-64 // g, 64 // g + 1))
+    return ("hindexed", lens, (disp * ext + shift).astype(np.int64), rec)
+
+
 def batch_specs(rng: np.random.Generator, nops: int, lo: int = 64, hi: int = 4 << 20):
     """`nops` independent layouts of float32 or bfloat16 with packed sizes
     log-uniform in [lo, hi] bytes: kind uniform over vector, indexed and

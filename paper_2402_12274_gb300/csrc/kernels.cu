@@ -111,6 +111,35 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) seg_kernel(Desc d, Op op
     }
 }
 
+// Record-major movement (rec_round): whole moves of an index list over a
+// short child table of runs, one record per lane per round of 32 records.
+// Warps take spans of `span` consecutive rounds (the search position carries
+// from one round to the next).  STAGE routes the packed side through a
+// per-warp shared-memory tile.
+template <int W, bool PACK, bool STAGE>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) rec_kernel(Desc d, Op op, int64_t nrec_elem,
+                                                                  int64_t rounds_elem, FastDiv div_rounds,
+                                                                  int64_t nrounds, int64_t span)
+{
+    extern __shared__ uint4 smem[];
+    __shared__ uint4 tiles[STAGE ? kWarps * kRecTile / 16 : 1];
+    const char *blob;
+    const DNode *nodes;
+    stage_desc(d, smem, blob, nodes);
+    allow_dependents();
+    prior_grids_wait();
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int64_t stride = (int64_t)gridDim.x * kWarps * span;
+    char *tile = reinterpret_cast<char *>(&tiles[STAGE ? (threadIdx.x >> 5) * (kRecTile / 16) : 0]);
+    Hint rh{-1, 0};
+    for (int64_t q0 = warp * span; q0 < nrounds; q0 += stride) {
+        const int64_t q1 = min(q0 + span, nrounds);
+        for (int64_t q = q0; q < q1; q++)
+            rec_round<W, PACK, STAGE>(op, nodes, blob, nrec_elem, rounds_elem, div_rounds, q, lane, rh, tile);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // batched movement: one persistent launch over many independent operations
 // ---------------------------------------------------------------------------
@@ -442,6 +471,24 @@ static MoveKernel pick_move(int W, bool pk16, bool wide)
     }
 }
 
+typedef void (*RecKernelFn)(Desc, Op, int64_t, int64_t, FastDiv, int64_t, int64_t);
+
+template <int W, bool PACK>
+static RecKernelFn pick_rec_w(bool stage)
+{
+    return stage ? rec_kernel<W, PACK, true> : rec_kernel<W, PACK, false>;
+}
+
+static RecKernelFn pick_rec(int W, bool pack, bool stage)
+{
+    switch (W) {
+    case 8: return pack ? pick_rec_w<8, true>(stage) : pick_rec_w<8, false>(stage);
+    case 4: return pack ? pick_rec_w<4, true>(stage) : pick_rec_w<4, false>(stage);
+    case 2: return pack ? pick_rec_w<2, true>(stage) : pick_rec_w<2, false>(stage);
+    default: return pack ? pick_rec_w<1, true>(stage) : pick_rec_w<1, false>(stage);
+    }
+}
+
 // The bulk kernels use more than the default 48 KiB of dynamic shared
 // memory (stages + staged descriptor); raised once per device.
 static void allow_bulk_smem(int dev)
@@ -502,6 +549,32 @@ static int launch_move(bool pack, dte_type t, const char *dblob, const void *use
     if (occ == 0) occ = occupancy(k, d.stage == STAGE_BLOB ? (size_t)kSmemBlob : smem);
     int64_t max_blocks = (int64_t)sm_count(dev) * occ;
     int64_t max_warps = max_blocks * kWarps;
+    int64_t rec_size = 0;
+    if (plan_seg(c, W, plan) && kRec && first == 0 && nbytes == count * c.size && rec_shape(c, &rec_size)) {
+        // an array of short records under a large index list: one record
+        // per lane per round
+        const int64_t nrec = c.size / rec_size;
+        const int64_t rounds_elem = (nrec + 31) / 32;
+        const int64_t nrounds = count * rounds_elem;
+        const bool stage = kRecStage && rec_size % 16 != 0 && rec_size <= kRecStageMaxSize &&
+                           p2addr(packed) >= 16 && (count == 1 || c.size % 16 == 0);
+        RecKernelFn rk = pick_rec(W, pack, stage);
+        static thread_local int rocc_cache[64][2][4][2][3];
+        int &rocc = rocc_cache[dev & 63][pack ? 1 : 0][W == 8 ? 0 : W == 4 ? 1 : W == 2 ? 2 : 3][stage ? 1 : 0]
+                              [d.stage];
+        if (rocc == 0) rocc = occupancy(rk, d.stage == STAGE_BLOB ? (size_t)kSmemBlob : smem);
+        const int64_t slots = (int64_t)sm_count(dev) * rocc * kWarps;
+        const int64_t span_rounds = std::max<int64_t>(1, std::min<int64_t>(8, nrounds / slots));
+        const int64_t units = (nrounds + span_rounds - 1) / span_rounds;
+        const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((units + kWarps - 1) / kWarps,
+                                                                      (int64_t)sm_count(dev) * rocc));
+        if (launch_overlapped(rk, (unsigned)blocks, kThreads, smem, stream, d, op, nrec, rounds_elem,
+                              make_div(rounds_elem), nrounds, span_rounds) != cudaSuccess) {
+            cudaGetLastError();
+            return DTE_ERR_CUDA;
+        }
+        return DTE_SUCCESS;
+    }
     if (plan_seg(c, W, plan)) {
         // short runs, small words: one decode per segment, cooperative copy
         typedef void (*SegKernel)(Desc, Op, int64_t, FastDiv, int64_t, int64_t, int64_t);

@@ -676,6 +676,160 @@ __device__ __forceinline__ void seg_round(const Op &op, const DNode *nodes, cons
 }
 
 // ---------------------------------------------------------------------------
+// record-major round
+// ---------------------------------------------------------------------------
+// A record is one copy of the child that a large index list repeats, when
+// that child is a short table of runs or a single run: an indexed or hindexed
+// type of a struct of basic blocks (or of a resized block), the
+// array-of-records layout.  Record-major movement gives each lane one whole
+// record per round of 32 records.  The warp finds the entries of the round's
+// records together, as shared_list_round does for segments, and then every
+// lane moves run j of its own record at the same time: the run lengths are
+// the same on every lane, so no lane waits on another's longer run, and the
+// per-round decode is shared by 32 records instead of 32 runs.
+#ifndef DTE_REC
+#define DTE_REC 1
+#endif
+constexpr bool kRec = DTE_REC != 0;     // build-time switch for the path
+constexpr int kRecMaxRuns = 16;         // runs of the child table
+constexpr int64_t kRecMaxSize = 256;    // packed bytes of one record
+// The packed side of a round (32 records, contiguous) can go through a
+// per-warp shared-memory tile: the lanes write their records into the tile
+// in copy words, then the warp moves the tile to or from global memory in
+// coalesced 16-byte accesses.  Used where the record's packed size is not a
+// multiple of 16 bytes (otherwise a lane's own accesses are already aligned)
+// and the round's packed start is 16-byte aligned.
+#ifndef DTE_REC_STAGE
+#define DTE_REC_STAGE 1
+#endif
+constexpr bool kRecStage = DTE_REC_STAGE != 0;
+constexpr int kRecStageMaxSize = 64;    // packed bytes of a record staged in the tile
+constexpr int kRecTile = 32 * kRecStageMaxSize;
+
+// Move one V-byte user word (V >= W) of a run: the user side takes one
+// V-byte access, the packed side (global memory, or the warp's shared tile
+// when PKSH) V/W words of W bytes.
+template <int V, int W, bool PACK, bool PKSH>
+__device__ __forceinline__ void rec_word(char *user, char *pk)
+{
+    using T = typename Word<W>::T;
+    union {
+        typename Word<V>::T v;
+        T w[V / W];
+    } x;
+    if (PACK) {
+        x.v = ldw<V>(user);
+#pragma unroll
+        for (int k = 0; k < V / W; k++) *reinterpret_cast<T *>(pk + k * W) = x.w[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < V / W; k++)
+            x.w[k] = PKSH ? *reinterpret_cast<const T *>(pk + k * W) : ldw<W>(pk + k * W);
+        *reinterpret_cast<typename Word<V>::T *>(user) = x.v;
+    }
+}
+
+// Move one run of n bytes (a multiple of W) between the user layout and the
+// packed side: the user side in the widest words its address allows (16,
+// then 8, 4 and 2 bytes while they fit), the packed side in W-byte words.
+template <int W, bool PACK, bool PKSH>
+__device__ __forceinline__ void rec_run(char *user, char *pk, int n)
+{
+    const unsigned ua = (unsigned)(uintptr_t)user;
+    int o = 0;
+    if (W < 16 && (ua & 15) == 0)
+        for (; o + 16 <= n; o += 16) rec_word<16, W, PACK, PKSH>(user + o, pk + o);
+    if (W < 8 && (ua & 7) == 0)
+        for (; o + 8 <= n; o += 8) rec_word<8, W, PACK, PKSH>(user + o, pk + o);
+    if (W < 4 && (ua & 3) == 0)
+        for (; o + 4 <= n; o += 4) rec_word<4, W, PACK, PKSH>(user + o, pk + o);
+    if (W < 2 && (ua & 1) == 0)
+        for (; o + 2 <= n; o += 2) rec_word<2, W, PACK, PKSH>(user + o, pk + o);
+    for (; o < n; o += W) rec_word<W, W, PACK, PKSH>(user + o, pk + o);
+}
+
+// Move nb packed bytes (a multiple of W) between global memory g (16-byte
+// aligned) and the warp's tile t: 16-byte accesses, then W-byte words for
+// the tail.
+template <int W, bool TO_GLOBAL>
+__device__ __forceinline__ void rec_tile_move(char *g, char *t, int nb, int lane)
+{
+    using T = typename Word<W>::T;
+    const int n16 = nb & ~15;
+    for (int o = lane * 16; o < n16; o += 512) {
+        if (TO_GLOBAL) *reinterpret_cast<uint4 *>(g + o) = *reinterpret_cast<const uint4 *>(t + o);
+        else *reinterpret_cast<uint4 *>(t + o) = ldw<16>(g + o);
+    }
+    for (int o = n16 + lane * W; o < nb; o += 32 * W) {
+        if (TO_GLOBAL) *reinterpret_cast<T *>(g + o) = *reinterpret_cast<const T *>(t + o);
+        else *reinterpret_cast<T *>(t + o) = ldw<W>(g + o);
+    }
+}
+
+// Round q of a whole move (never a packed window): records local0 ..
+// local0 + 31 of element e, where q = e * rounds_elem + local0 / 32, clipped
+// to the element's nrec_elem records.  Entry b of the root holds records
+// pbytes[b] / size(child) onward (every entry has at least one record and
+// nothing merges), so lane j loads entry b0 + j's prefix and displacement,
+// one OR-reduction marks the entries that start inside the round, and lane l
+// takes its entry's values by shuffle.  `rh` is the warp's search position in
+// the root list; `tile` is the warp's shared tile when STAGE.
+template <int W, bool PACK, bool STAGE>
+__device__ __forceinline__ void rec_round(const Op &op, const DNode *nodes, const char *blob, int64_t nrec_elem,
+                                          int64_t rounds_elem, const FastDiv &div_rounds, int64_t q, int lane,
+                                          Hint &rh, char *tile)
+{
+    const unsigned FULL = 0xffffffffu;
+    const DNode &R = nodes[op.root];
+    const DNode &C = nodes[R.child];
+    const int64_t e = fdiv(q, div_rounds);
+    const int64_t local0 = (q - e * rounds_elem) * 32;
+    const int nvalid = (int)min((int64_t)32, nrec_elem - local0);
+    const int64_t *pb = arr<int64_t>(blob, R.a_pbytes);
+    const int64_t *dv = arr<int64_t>(blob, R.a_disp);
+    const int64_t b0 = find_le(pb, R.count, local0 * C.size, rh, op.root);
+    const int64_t bj = b0 + lane;
+    const int64_t sj = bj <= R.count ? fdiv(pb[bj], C.div_size) : INT64_MAX;  // first record of entry bj
+    const int64_t dj = bj < R.count ? dv[bj] : 0;
+    const int64_t o = sj - local0;
+    const unsigned starts = __reduce_or_sync(FULL, (lane > 0 && o > 0 && o < 32) ? 1u << (int)o : 0u);
+    const int jl = __popc(starts & (FULL >> (31 - lane)));
+    const int64_t de = __shfl_sync(FULL, dj, jl);
+    const int64_t se = __shfl_sync(FULL, sj, jl);
+    rh.b = b0 + __shfl_sync(FULL, jl, nvalid - 1);
+    // the lane's record: user address of the child copy, packed stream offset
+    const int64_t r = local0 + lane;
+    const int64_t ud = e * op.extent + R.base + de + (r - se) * R.stride + C.base;
+    const int64_t pround = e * op.esize + local0 * C.size;
+    const int csize = (int)C.size;
+    const int nb = nvalid * csize;
+    char *user = (PACK ? const_cast<char *>(op.user_in) : op.user_out) + ud;
+    char *gpk = (PACK ? op.packed_out : const_cast<char *>(op.packed_in)) + pround;
+    char *pk = STAGE ? tile + lane * csize : gpk + lane * csize;
+    if (STAGE && !PACK) {
+        rec_tile_move<W, false>(gpk, tile, nb, lane);
+        __syncwarp();
+    }
+    if (C.kind == NK_RUN) {
+        if (lane < nvalid) rec_run<W, PACK, STAGE>(user, pk, (int)C.len);
+    } else {
+        const int64_t *cpb = arr<int64_t>(blob, C.a_pbytes);
+        const int64_t *cdv = arr<int64_t>(blob, C.a_disp);
+#pragma unroll 1
+        for (int j = 0; j < (int)C.count; j++) {
+            const int64_t p = cpb[j];
+            const int n = (int)(cpb[j + 1] - p);
+            if (lane < nvalid) rec_run<W, PACK, STAGE>(user + cdv[j], pk + p, n);
+        }
+    }
+    if (STAGE) {
+        __syncwarp();
+        if (PACK) rec_tile_move<W, true>(gpk, tile, nb, lane);
+        __syncwarp();  // the tile is refilled by the next round
+    }
+}
+
+// ---------------------------------------------------------------------------
 // batch op records
 // ---------------------------------------------------------------------------
 struct BatchOp {
@@ -775,6 +929,25 @@ static int word_of(const Committed &c, int64_t extent, int64_t count, const void
     int64_t W = std::min<int64_t>(c.align, std::min(p2addr(user), p2addr(packed)));
     if (count > 1) W = std::min(W, p2v(extent));
     return (int)W;
+}
+
+// Whether whole moves of a type can go record-major (rec_round): its root is
+// a large index list of one shared child with no merging (the conditions of
+// shared_list_root), and that child is a table of at most kRecMaxRuns runs,
+// or one run, of at most kRecMaxSize packed bytes.  *child_size: packed bytes
+// of one record.
+static bool rec_shape(const Committed &c, int64_t *child_size)
+{
+    const DNode *n = c.nodes();
+    const DNode &R = n[c.root];
+    if (R.kind != NK_LIST || !(R.flags & NF_SHARED) || (R.flags & (NF_RUNS | NF_PSEGS | NF_XMERGE | NF_EMERGE)) ||
+        R.a_eflags != 0 || R.count <= 32 || R.child < 0)
+        return false;
+    const DNode &C = n[R.child];
+    const bool table = C.kind == NK_LIST && (C.flags & NF_RUNS) && C.count >= 1 && C.count <= kRecMaxRuns;
+    if (!(table || C.kind == NK_RUN) || C.size <= 0 || C.size > kRecMaxSize) return false;
+    *child_size = C.size;
+    return true;
 }
 
 static Op make_op(const Committed &c, int64_t extent, const void *user, void *packed, int64_t count)

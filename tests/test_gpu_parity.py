@@ -300,6 +300,20 @@ def test_record_indexed_full_size():
     check_record_indexed(1 << 22)
 
 
+def test_record_major_layouts():
+    # arrays of records under index lists of more than 32 entries move one
+    # whole record per lane (record-major): random records of 1-6 blocks and
+    # single resized blocks, every copy word, 1-3 elements, aligned buffers
+    # (the packed side of a round staged in shared memory where the record is
+    # not a multiple of 16 bytes) and misaligned ones (not staged)
+    rng = np.random.default_rng(206)
+    for _ in range(150):
+        spec = inputs.record_variety_spec(rng, int(rng.choice([33, 100, 1000, 5000])))
+        count = int(rng.integers(1, 4))
+        check_move(spec, count, rng, misalign=False)
+        check_move(spec, count, rng)
+
+
 def check_record_indexed(nblocks):
     rng = np.random.default_rng(3)
     spec = inputs.record_indexed_spec(rng, nblocks)

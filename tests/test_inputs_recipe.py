@@ -28,6 +28,28 @@ def test_record_layout_recipe():
     assert d.tolist() == [0, 16] and l.tolist() == [12, 40]
 
 
+def test_record_variety_recipe():
+    # records of 1-6 blocks (or one block) at a grain of 1-8 bytes, under an
+    # index list of sorted, non-overlapping blocks of whole records
+    rng = np.random.default_rng(206)
+    seen = set()
+    for _ in range(200):
+        kind, bl, disp, rec = inputs.record_variety_spec(rng, 100)
+        assert kind in ("indexed", "hindexed") and bl.size == disp.size == 100 and bl.min() >= 1
+        r = oracle.from_spec(rec)
+        assert r.size > 0 and r.lb == 0 and r.true_lb == 0 and r.extent >= r.true_extent
+        d, l = r.iov()
+        assert d.size <= 6 and np.all(d[1:] >= d[:-1] + l[:-1])  # runs in order, disjoint
+        ext = r.extent if kind == "indexed" else 1
+        lo = disp * ext
+        hi = lo + (bl - 1) * r.extent + r.true_extent
+        assert np.all(lo[1:] >= hi[:-1])  # whole records never overlap
+        seen.add((kind, rec[0], int(np.gcd.reduce(np.concatenate([d, l, [r.extent]])) % 16)))
+    assert {k for k, _, _ in seen} == {"indexed", "hindexed"}
+    assert {c for _, c, _ in seen} == {"struct", "resized", "contig"}
+    assert {g for _, _, g in seen} >= {1, 2, 4, 8}
+
+
 def test_batch_mix_recipe():
     rng = np.random.default_rng(4)
     specs = inputs.batch_specs(rng, 3000)
@@ -95,6 +117,7 @@ def test_generators_are_pure_functions_of_the_seed():
 
     for f in (lambda r: inputs.record_indexed_spec(r, 100), lambda r: inputs.batch_specs(r, 50),
               lambda r: inputs.halo_indexed_specs(r, n=6, g=2), lambda r: [inputs.random_spec(r) for _ in range(20)],
-              lambda r: [inputs.random_darray_spec(r) for _ in range(20)]):
+              lambda r: [inputs.random_darray_spec(r) for _ in range(20)],
+              lambda r: [inputs.record_variety_spec(r, 40) for _ in range(20)]):
         assert same(f(np.random.default_rng(11)), f(np.random.default_rng(11)))
     assert np.array_equal(inputs.random_bytes(1000, 7), inputs.random_bytes(1000, 7))
