@@ -114,15 +114,21 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) seg_kernel(Desc d, Op op
 // Record-major movement (rec_round): whole moves of an index list over a
 // short child table of runs, one record per lane per round of 32 records.
 // Warps take spans of `span` consecutive rounds (the search position carries
-// from one round to the next).  STAGE routes the packed side through a
-// per-warp shared-memory tile.
+// from one round to the next).  STAGE routes the packed side through
+// per-warp shared-memory tiles; a staged unpack keeps two, so that the next
+// round's packed bytes are fetched while the current round is scattered.
+// CTAs per SM the record-major kernels are built for, by direction (records
+// of 2^22 blocks, one box: pack 3.74 / 3.96 / 3.30 TB/s at 4 / 6 / 8, unpack
+// 2.30 / 2.24 / 2.14).
+constexpr int kRecMinBlocksPack = 6;
+constexpr int kRecMinBlocksUnpack = 4;
 template <int W, bool PACK, bool STAGE>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) rec_kernel(Desc d, Op op, int64_t nrec_elem,
-                                                                  int64_t rounds_elem, FastDiv div_rounds,
-                                                                  int64_t nrounds, int64_t span)
+__global__ void __launch_bounds__(kThreads, PACK ? kRecMinBlocksPack : kRecMinBlocksUnpack)
+    rec_kernel(Desc d, Op op, int64_t nrec_elem, int64_t rounds_elem, FastDiv div_rounds, int64_t nrounds, int64_t span)
 {
+    constexpr int kTilesPerWarp = STAGE ? (PACK ? 1 : 2) : 0;
     extern __shared__ uint4 smem[];
-    __shared__ uint4 tiles[STAGE ? kWarps * kRecTile / 16 : 1];
+    __shared__ uint4 tiles[STAGE ? kWarps * kTilesPerWarp * kRecTile / 16 : 1];
     const char *blob;
     const DNode *nodes;
     stage_desc(d, smem, blob, nodes);
@@ -131,12 +137,16 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) rec_kernel(Desc d, Op op
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int64_t stride = (int64_t)gridDim.x * kWarps * span;
-    char *tile = reinterpret_cast<char *>(&tiles[STAGE ? (threadIdx.x >> 5) * (kRecTile / 16) : 0]);
+    char *tile = reinterpret_cast<char *>(&tiles[STAGE ? (threadIdx.x >> 5) * (kTilesPerWarp * kRecTile / 16) : 0]);
     Hint rh{-1, 0};
     for (int64_t q0 = warp * span; q0 < nrounds; q0 += stride) {
         const int64_t q1 = min(q0 + span, nrounds);
-        for (int64_t q = q0; q < q1; q++)
-            rec_round<W, PACK, STAGE>(op, nodes, blob, nrec_elem, rounds_elem, div_rounds, q, lane, rh, tile);
+        if (STAGE && !PACK) {
+            rec_unpack_rounds<W>(op, nodes, blob, nrec_elem, rounds_elem, div_rounds, q0, q1, lane, rh, tile);
+        } else {
+            for (int64_t q = q0; q < q1; q++)
+                rec_round<W, PACK, STAGE>(op, nodes, blob, nrec_elem, rounds_elem, div_rounds, q, lane, rh, tile);
+        }
     }
 }
 

@@ -766,66 +766,156 @@ __device__ __forceinline__ void rec_tile_move(char *g, char *t, int nb, int lane
     }
 }
 
-// Round q of a whole move (never a packed window): records local0 ..
-// local0 + 31 of element e, where q = e * rounds_elem + local0 / 32, clipped
-// to the element's nrec_elem records.  Entry b of the root holds records
+// Where round q of a whole move (never a packed window) sits: records
+// local0 .. local0 + 31 of element e, where q = e * rounds_elem + local0 / 32,
+// clipped to the element's nrec_elem records.
+struct RecPlace {
+    int64_t e;
+    int64_t local0;
+    int64_t pround;  // packed stream offset of the round's first byte
+    int nvalid;      // records in the round
+};
+
+__device__ __forceinline__ RecPlace rec_place(const Op &op, const DNode &C, int64_t nrec_elem, int64_t rounds_elem,
+                                              const FastDiv &div_rounds, int64_t q)
+{
+    RecPlace r;
+    r.e = fdiv(q, div_rounds);
+    r.local0 = (q - r.e * rounds_elem) * 32;
+    r.nvalid = (int)min((int64_t)32, nrec_elem - r.local0);
+    r.pround = r.e * op.esize + r.local0 * C.size;
+    return r;
+}
+
+// User displacement of the lane's record in round `at` (lanes past nvalid
+// get a value that is never used).  Entry b of the root holds records
 // pbytes[b] / size(child) onward (every entry has at least one record and
 // nothing merges), so lane j loads entry b0 + j's prefix and displacement,
 // one OR-reduction marks the entries that start inside the round, and lane l
-// takes its entry's values by shuffle.  `rh` is the warp's search position in
-// the root list; `tile` is the warp's shared tile when STAGE.
+// takes its entry's values by shuffle.  `rh` is the warp's search position
+// in the root list.
+__device__ __forceinline__ int64_t rec_locate(const Op &op, const DNode &R, const DNode &C, const char *blob,
+                                              const RecPlace &at, int lane, Hint &rh)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int64_t *pb = arr<int64_t>(blob, R.a_pbytes);
+    const int64_t *dv = arr<int64_t>(blob, R.a_disp);
+    const int64_t b0 = find_le(pb, R.count, at.local0 * C.size, rh, op.root);
+    const int64_t bj = b0 + lane;
+    const int64_t sj = bj <= R.count ? fdiv(pb[bj], C.div_size) : INT64_MAX;  // first record of entry bj
+    const int64_t dj = bj < R.count ? dv[bj] : 0;
+    const int64_t o = sj - at.local0;
+    const unsigned starts = __reduce_or_sync(FULL, (lane > 0 && o > 0 && o < 32) ? 1u << (int)o : 0u);
+    const int jl = __popc(starts & (FULL >> (31 - lane)));
+    const int64_t de = __shfl_sync(FULL, dj, jl);
+    const int64_t se = __shfl_sync(FULL, sj, jl);
+    rh.b = b0 + __shfl_sync(FULL, jl, at.nvalid - 1);
+    return at.e * op.extent + R.base + de + (at.local0 + lane - se) * R.stride + C.base;
+}
+
+// Move the runs of the lane's record between the user layout (user: the
+// record's child copy) and its packed bytes pk (global memory, or the warp's
+// tile when PKSH), run j of every lane at the same time.
+template <int W, bool PACK, bool PKSH>
+__device__ __forceinline__ void rec_runs(const DNode &C, const char *blob, char *user, char *pk, bool live)
+{
+    if (C.kind == NK_RUN) {
+        if (live) rec_run<W, PACK, PKSH>(user, pk, (int)C.len);
+        return;
+    }
+    const int64_t *cpb = arr<int64_t>(blob, C.a_pbytes);
+    const int64_t *cdv = arr<int64_t>(blob, C.a_disp);
+#pragma unroll 1
+    for (int j = 0; j < (int)C.count; j++) {
+        const int64_t p = cpb[j];
+        const int n = (int)(cpb[j + 1] - p);
+        if (live) rec_run<W, PACK, PKSH>(user + cdv[j], pk + p, n);
+    }
+}
+
+// One round, moved directly (no tile), or staged through the warp's tile
+// `tile` when STAGE.
 template <int W, bool PACK, bool STAGE>
 __device__ __forceinline__ void rec_round(const Op &op, const DNode *nodes, const char *blob, int64_t nrec_elem,
                                           int64_t rounds_elem, const FastDiv &div_rounds, int64_t q, int lane,
                                           Hint &rh, char *tile)
 {
-    const unsigned FULL = 0xffffffffu;
     const DNode &R = nodes[op.root];
     const DNode &C = nodes[R.child];
-    const int64_t e = fdiv(q, div_rounds);
-    const int64_t local0 = (q - e * rounds_elem) * 32;
-    const int nvalid = (int)min((int64_t)32, nrec_elem - local0);
-    const int64_t *pb = arr<int64_t>(blob, R.a_pbytes);
-    const int64_t *dv = arr<int64_t>(blob, R.a_disp);
-    const int64_t b0 = find_le(pb, R.count, local0 * C.size, rh, op.root);
-    const int64_t bj = b0 + lane;
-    const int64_t sj = bj <= R.count ? fdiv(pb[bj], C.div_size) : INT64_MAX;  // first record of entry bj
-    const int64_t dj = bj < R.count ? dv[bj] : 0;
-    const int64_t o = sj - local0;
-    const unsigned starts = __reduce_or_sync(FULL, (lane > 0 && o > 0 && o < 32) ? 1u << (int)o : 0u);
-    const int jl = __popc(starts & (FULL >> (31 - lane)));
-    const int64_t de = __shfl_sync(FULL, dj, jl);
-    const int64_t se = __shfl_sync(FULL, sj, jl);
-    rh.b = b0 + __shfl_sync(FULL, jl, nvalid - 1);
-    // the lane's record: user address of the child copy, packed stream offset
-    const int64_t r = local0 + lane;
-    const int64_t ud = e * op.extent + R.base + de + (r - se) * R.stride + C.base;
-    const int64_t pround = e * op.esize + local0 * C.size;
+    const RecPlace at = rec_place(op, C, nrec_elem, rounds_elem, div_rounds, q);
+    const int64_t ud = rec_locate(op, R, C, blob, at, lane, rh);
     const int csize = (int)C.size;
-    const int nb = nvalid * csize;
+    const int nb = at.nvalid * csize;
     char *user = (PACK ? const_cast<char *>(op.user_in) : op.user_out) + ud;
-    char *gpk = (PACK ? op.packed_out : const_cast<char *>(op.packed_in)) + pround;
+    char *gpk = (PACK ? op.packed_out : const_cast<char *>(op.packed_in)) + at.pround;
     char *pk = STAGE ? tile + lane * csize : gpk + lane * csize;
     if (STAGE && !PACK) {
         rec_tile_move<W, false>(gpk, tile, nb, lane);
         __syncwarp();
     }
-    if (C.kind == NK_RUN) {
-        if (lane < nvalid) rec_run<W, PACK, STAGE>(user, pk, (int)C.len);
-    } else {
-        const int64_t *cpb = arr<int64_t>(blob, C.a_pbytes);
-        const int64_t *cdv = arr<int64_t>(blob, C.a_disp);
-#pragma unroll 1
-        for (int j = 0; j < (int)C.count; j++) {
-            const int64_t p = cpb[j];
-            const int n = (int)(cpb[j + 1] - p);
-            if (lane < nvalid) rec_run<W, PACK, STAGE>(user + cdv[j], pk + p, n);
-        }
-    }
+    rec_runs<W, PACK, STAGE>(C, blob, user, pk, lane < at.nvalid);
     if (STAGE) {
         __syncwarp();
         if (PACK) rec_tile_move<W, true>(gpk, tile, nb, lane);
         __syncwarp();  // the tile is refilled by the next round
+    }
+}
+
+// Asynchronous 16-byte copies from global into shared memory (cp.async;
+// completion per thread by commit and wait groups).
+__device__ __forceinline__ void cp_async16(char *sdst, const char *gsrc)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// The 16-byte part of a round's packed bytes (global, 16-byte aligned) into
+// a tile, asynchronously; the tail (nb not a multiple of 16) is loaded when
+// the round is scattered.
+__device__ __forceinline__ void rec_tile_fetch(const char *g, char *t, int nb, int lane)
+{
+    const int n16 = nb & ~15;
+    for (int o = lane * 16; o < n16; o += 512) cp_async16(t + o, g + o);
+}
+
+// Staged unpack of the warp's rounds [q0, q1) with two tiles: the packed
+// bytes of the next round are in flight (cp.async) while the entries of the
+// current round are searched and its records scattered.  A round's packed
+// bytes depend on its position alone, so the copy can start before the
+// search.
+template <int W>
+__device__ __forceinline__ void rec_unpack_rounds(const Op &op, const DNode *nodes, const char *blob,
+                                                  int64_t nrec_elem, int64_t rounds_elem, const FastDiv &div_rounds,
+                                                  int64_t q0, int64_t q1, int lane, Hint &rh, char *tiles)
+{
+    using T = typename Word<W>::T;
+    const DNode &R = nodes[op.root];
+    const DNode &C = nodes[R.child];
+    const int csize = (int)C.size;
+    {
+        const RecPlace first = rec_place(op, C, nrec_elem, rounds_elem, div_rounds, q0);
+        rec_tile_fetch(op.packed_in + first.pround, tiles, first.nvalid * csize, lane);
+    }
+    cp_async_commit();
+    for (int64_t q = q0; q < q1; q++) {
+        char *tile = tiles + ((q - q0) & 1) * kRecTile;
+        if (q + 1 < q1) {
+            const RecPlace nx = rec_place(op, C, nrec_elem, rounds_elem, div_rounds, q + 1);
+            rec_tile_fetch(op.packed_in + nx.pround, tiles + ((q + 1 - q0) & 1) * kRecTile, nx.nvalid * csize, lane);
+        }
+        cp_async_commit();  // an empty group when there is no next round
+        const RecPlace at = rec_place(op, C, nrec_elem, rounds_elem, div_rounds, q);
+        const int64_t ud = rec_locate(op, R, C, blob, at, lane, rh);
+        const int nb = at.nvalid * csize;
+        const char *g = op.packed_in + at.pround;
+        for (int o = (nb & ~15) + lane * W; o < nb; o += 32 * W)
+            *reinterpret_cast<T *>(tile + o) = ldw<W>(g + o);
+        cp_async_wait_prev();  // this round's tile has landed
+        __syncwarp();
+        rec_runs<W, false, true>(C, blob, op.user_out + ud, tile + lane * csize, lane < at.nvalid);
+        __syncwarp();  // the tile is refilled two rounds on
     }
 }
 
