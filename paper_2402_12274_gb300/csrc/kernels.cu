@@ -290,6 +290,42 @@ struct IovArgs {
     int64_t per_warp;
 };
 
+// Segments s0 .. s0 + nvalid - 1 (warp-uniform, 1 <= nvalid <= 32) of the
+// count-level segment list: lane l < nvalid gets the displacement and length
+// of segment s0 + l.  A round inside one element of a root index list over
+// one shared child is decoded by the warp together (shared_list_round: one
+// search, coalesced entry loads, shuffles); other rounds lane by lane.
+__device__ __forceinline__ void iov_round(const Op &op, const DNode *nodes, const char *blob, int64_t nseg,
+                                          const FastDiv &div_nseg, int64_t s0, int nvalid, int lane, Hint &h,
+                                          Hint &rh, int64_t &disp, int64_t &len)
+{
+    const DNode &R = nodes[op.root];
+    const int64_t e0 = fdiv(s0, div_nseg);
+    const int64_t local0 = s0 - e0 * nseg;
+    disp = 0;
+    len = 0;
+    if (shared_list_root(R) && local0 + nvalid <= nseg) {
+        int64_t ps;
+        shared_list_round(op, nodes, blob, R, e0, local0, nvalid, lane, rh, h, disp, len, ps);
+    } else if (lane < nvalid) {
+        const int64_t sl = s0 + lane;
+        const int64_t e = fdiv(sl, div_nseg);
+        disp = e * op.extent;
+        decode_seg(nodes, blob, op.root, sl - e * nseg, disp, len, h);
+    }
+}
+
+// Only the fields iov_round reads: the root and the element stride.
+__device__ __forceinline__ Op iov_op(int32_t root, int64_t extent)
+{
+    Op op = {};
+    op.root = root;
+    op.extent = extent;
+    return op;
+}
+
+// Warp w writes segments [w * per_warp, (w + 1) * per_warp) of the request
+// (per_warp a multiple of 32) in rounds of 32 consecutive segments.
 __global__ void __launch_bounds__(kThreads) iov_kernel(Desc d, IovArgs a)
 {
     extern __shared__ uint4 smem[];
@@ -300,16 +336,18 @@ __global__ void __launch_bounds__(kThreads) iov_kernel(Desc d, IovArgs a)
     const int64_t warp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int64_t k0 = warp * a.per_warp;
     const int64_t k1 = min(k0 + a.per_warp, a.n);
-    Hint h{-1, 0};
-    for (int64_t k = k0 + lane; k < k1; k += 32) {
-        int64_t s = a.first + k;
-        int64_t e = fdiv(s, a.div_nseg);
-        int64_t dd = e * a.extent, len = 0;
-        decode_seg(nodes, blob, d.root, s - e * a.nseg, dd, len, h);
-        dte_iov v;
-        v.iov_base = (void *)(a.base + dd);
-        v.iov_len = len;
-        a.out[k] = v;
+    const Op op = iov_op(d.root, a.extent);
+    Hint h{-1, 0}, rh{-1, 0};
+    for (int64_t kb = k0; kb < k1; kb += 32) {
+        const int nvalid = (int)min((int64_t)32, k1 - kb);
+        int64_t dd, len;
+        iov_round(op, nodes, blob, a.nseg, a.div_nseg, a.first + kb, nvalid, lane, h, rh, dd, len);
+        if (lane < nvalid) {
+            dte_iov v;
+            v.iov_base = (void *)(a.base + dd);
+            v.iov_len = len;
+            a.out[kb + lane] = v;
+        }
     }
     if (a.actual && blockIdx.x == 0 && threadIdx.x == 0) *a.actual = a.n;
 }
@@ -365,21 +403,52 @@ __global__ void __launch_bounds__(kThreads) at_bytes_first_kernel(Desc d, int64_
     }
 }
 
+// Second pass: item it of the nq x maxlen output is segment first[q] + i of
+// query q = it / maxlen (one element: segments below nseg).  Warp w fills
+// items [w * per_warp, (w + 1) * per_warp) (per_warp a multiple of 32) in
+// rounds of 32: a round inside one query is 32 consecutive segments and goes
+// through iov_round; a round across two queries is decoded lane by lane.  A
+// grid-wide stride would instead send every lookup to another query and
+// search the index table from far away.
 __global__ void __launch_bounds__(kThreads) at_bytes_fill_kernel(Desc d, int64_t nq, int64_t maxlen,
                                                                  FastDiv div_max, const int64_t *first,
                                                                  const int64_t *actual, dte_iov *out,
-                                                                 const char *base)
+                                                                 const char *base, int64_t nseg, FastDiv div_nseg,
+                                                                 int64_t per_warp)
 {
     extern __shared__ uint4 smem[];
     const char *blob;
     const DNode *nodes;
     stage_desc(d, smem, blob, nodes);
-    Hint h{-1, 0};
-    int64_t total = nq * maxlen;
-    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < total;
-         it += (int64_t)gridDim.x * blockDim.x) {
-        int64_t q = fdiv(it, div_max);
-        int64_t i = it - q * maxlen;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int64_t total = nq * maxlen;
+    const int64_t i0 = warp * per_warp;
+    const int64_t i1 = min(i0 + per_warp, total);
+    const Op op = iov_op(d.root, 0);
+    Hint h{-1, 0}, rh{-1, 0};
+    for (int64_t ib = i0; ib < i1; ib += 32) {
+        const int n = (int)min((int64_t)32, i1 - ib);
+        const int64_t qb = fdiv(ib, div_max);
+        const int64_t jb = ib - qb * maxlen;
+        if (jb + n <= maxlen) {
+            // one query: segments first[qb] + jb onward, cut at its count
+            const int nv = (int)max((int64_t)0, min((int64_t)n, actual[qb] - jb));
+            if (nv == 0) continue;
+            int64_t dd, len;
+            iov_round(op, nodes, blob, nseg, div_nseg, first[qb] + jb, nv, lane, h, rh, dd, len);
+            if (lane < nv) {
+                dte_iov v;
+                v.iov_base = (void *)(base + dd);
+                v.iov_len = len;
+                out[ib + lane] = v;
+            }
+            continue;
+        }
+        const int64_t it = ib + lane;
+        if (lane >= n) continue;
+        const int64_t q = fdiv(it, div_max);
+        const int64_t i = it - q * maxlen;
         if (i >= actual[q]) continue;
         int64_t dd = 0, len = 0;
         decode_seg(nodes, blob, d.root, first[q] + i, dd, len, h);
@@ -1233,9 +1302,13 @@ int dte_type_iov_at_bytes_async(dte_type type, int64_t n, const int64_t *d_offse
         if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
         if (total > 0) {
             FastDiv dm = make_div(max_iov_len);
-            int64_t b2 = std::min<int64_t>((total + kThreads - 1) / kThreads, sms * 4);
+            const int64_t warps_needed = (total + 127) / 128;
+            const int64_t b2 = std::max<int64_t>(1, std::min<int64_t>((warps_needed + kWarps - 1) / kWarps, sms * 4));
+            int64_t per_warp = (total + b2 * kWarps - 1) / (b2 * kWarps);
+            per_warp = (per_warp + 31) / 32 * 32;
             at_bytes_fill_kernel<<<(unsigned)b2, kThreads, smem, (cudaStream_t)stream>>>(
-                d, n, max_iov_len, dm, d_first, d_actual, d_iov, (const char *)base);
+                d, n, max_iov_len, dm, d_first, d_actual, d_iov, (const char *)base, c.nseg,
+                c.nodes()[c.root].div_nseg, per_warp);
             if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
         }
         note_use(type, dev, stream);

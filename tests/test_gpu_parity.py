@@ -220,6 +220,37 @@ def test_iov_len_and_at_bytes_device():
             assert np.array_equal(got[:, 0], sd[k:k + a[q]]) and np.array_equal(got[:, 1], sl[k:k + a[q]])
 
 
+def test_list_iov_device_rounds():
+    # large index lists over one shared child: the iov kernels decode rounds
+    # of 32 segments by the warp together; rounds that straddle two elements
+    # (iov) or two queries (at_bytes with 37 segments per query) go lane by lane
+    rng = np.random.default_rng(207)
+    s = torch.cuda.current_stream().cuda_stream
+    for _ in range(40):
+        spec = inputs.record_variety_spec(rng, int(rng.choice([33, 300, 2000])))
+        t, o = both(spec)
+        count = int(rng.integers(1, 4))
+        total = count * o.iov_count()
+        first = int(rng.integers(0, max(1, total // 3)))
+        iov_check(t, o, count, first, int(rng.integers(1, total - first + 5)))
+        sd, sl = o.iov()
+        offs = rng.integers(0, o.size, 24).astype(np.int64)
+        for m in (37, 64):
+            d_o = torch.from_numpy(offs).to(DEV)
+            d_iov = torch.zeros((offs.size * m, 2), dtype=torch.int64, device=DEV)
+            d_f = torch.empty_like(d_o)
+            d_a = torch.empty_like(d_o)
+            dte.dte_type_iov_at_bytes_async(t.h, offs.size, d_o.data_ptr(), m, d_iov.data_ptr(), d_f.data_ptr(),
+                                            d_a.data_ptr(), 0, s)
+            torch.cuda.synchronize()
+            f, a, iv = d_f.cpu().numpy(), d_a.cpu().numpy(), d_iov.cpu().numpy()
+            for q, b in enumerate(offs):
+                k = o.iov_len(int(b))[0]
+                assert f[q] == k and a[q] == min(m, len(sd) - k)
+                got = iv[q * m: q * m + a[q]]
+                assert np.array_equal(got[:, 0], sd[k:k + a[q]]) and np.array_equal(got[:, 1], sl[k:k + a[q]])
+
+
 # --------------------------------------------------------------------------
 # workload layouts
 # --------------------------------------------------------------------------
