@@ -220,6 +220,34 @@ def test_iov_len_and_at_bytes_device():
             assert np.array_equal(got[:, 0], sd[k:k + a[q]]) and np.array_equal(got[:, 1], sl[k:k + a[q]])
 
 
+def test_record_block_gather_layouts():
+    # arrays of records whose starts are all one offset modulo 16 (record
+    # extents and byte displacements multiples of 16), user buffers shifted
+    # by 0-15 bytes against aligned packed buffers: the record-major kernels
+    # with their staged tiles at every copy word, pack and unpack
+    rng = np.random.default_rng(208)
+    for _ in range(60):
+        kind, lens, disp, rec = inputs.record_variety_spec(rng, int(rng.choice([40, 700, 3000])))
+        ext = oracle.from_spec(rec).extent
+        e16 = -(-ext // 16) * 16 + 16 * int(rng.integers(0, 2))
+        rec16 = ("resized", 0, e16, rec)
+        units = np.cumsum(np.concatenate([[0], lens[:-1] + 1]))  # one-record gaps keep blocks apart
+        spec = ("indexed", lens, units.astype(np.int64), rec16) if kind == "indexed" else \
+            ("hindexed", lens, (units * e16).astype(np.int64), rec16)
+        t, o = both(spec)
+        count = int(rng.integers(1, 4))
+        lo, hi = span_of(o, count)
+        for shift in (0, int(rng.integers(1, 16))):
+            base = -lo + shift
+            span = hi - lo + shift + 1
+            src = rng.integers(0, 256, span, dtype=np.uint8)
+            ref = o.pack(src, count, base)
+            assert np.array_equal(gpu_pack(t, src, count, base, 0), ref), (spec, count, shift)
+            want = np.full(span, SENT, np.uint8)
+            o.unpack(ref, count, want, base)
+            assert np.array_equal(gpu_unpack(t, ref, count, span, base, 0), want), (spec, count, shift)
+
+
 def test_list_iov_device_rounds():
     # large index lists over one shared child: the iov kernels decode rounds
     # of 32 segments by the warp together; rounds that straddle two elements
