@@ -288,6 +288,15 @@ struct IovArgs {
     FastDiv div_nseg;
     int64_t extent;
     int64_t per_warp;
+    // record-major lists (arrays of short records, rec_shape): runs per
+    // record (0: off), records per element and their rounds of 32, and the
+    // request's first round; per_warp then counts rounds
+    int64_t rec_runs;
+    int64_t nrec_elem;
+    int64_t rounds_elem;
+    FastDiv div_rounds;
+    int64_t q_first;
+    int64_t nrounds;
 };
 
 // Segments s0 .. s0 + nvalid - 1 (warp-uniform, 1 <= nvalid <= 32) of the
@@ -338,6 +347,33 @@ __global__ void __launch_bounds__(kThreads) iov_kernel(Desc d, IovArgs a)
     const int64_t k1 = min(k0 + a.per_warp, a.n);
     const Op op = iov_op(d.root, a.extent);
     Hint h{-1, 0}, rh{-1, 0};
+    if (a.rec_runs > 0) {
+        // one record per lane per round of 32 records (rec_locate); segment
+        // k of the list is run k % runs of record k / runs
+        const DNode &R = nodes[d.root];
+        const DNode &C = nodes[R.child];
+        const int64_t *cpb = C.kind == NK_RUN ? nullptr : arr<int64_t>(blob, C.a_pbytes);
+        const int64_t *cdv = C.kind == NK_RUN ? nullptr : arr<int64_t>(blob, C.a_disp);
+        const int64_t q0 = a.q_first + warp * a.per_warp;
+        const int64_t q1 = min(q0 + a.per_warp, a.q_first + a.nrounds);
+        for (int64_t q = q0; q < q1; q++) {
+            const RecPlace at = rec_place(op, C, a.nrec_elem, a.rounds_elem, a.div_rounds, q);
+            const int64_t ud = rec_locate(op, R, C, blob, at, lane, rh);
+            if (lane >= at.nvalid) continue;
+            const int64_t k0r = (at.e * a.nrec_elem + at.local0 + lane) * a.rec_runs - a.first;
+#pragma unroll 1
+            for (int j = 0; j < (int)a.rec_runs; j++) {
+                const int64_t k = k0r + j;
+                if (k < 0 || k >= a.n) continue;
+                dte_iov v;
+                v.iov_base = (void *)(a.base + ud + (cdv ? cdv[j] : 0));
+                v.iov_len = cpb ? cpb[j + 1] - cpb[j] : C.len;
+                a.out[k] = v;
+            }
+        }
+        if (a.actual && blockIdx.x == 0 && threadIdx.x == 0) *a.actual = a.n;
+        return;
+    }
     for (int64_t kb = k0; kb < k1; kb += 32) {
         const int nvalid = (int)min((int64_t)32, k1 - kb);
         int64_t dd, len;
@@ -1231,11 +1267,38 @@ int dte_type_iov_async(dte_type type, int64_t count, int64_t iov_offset, dte_iov
         a.nseg = c.nseg;
         a.div_nseg = c.nodes()[c.root].div_nseg;
         a.extent = type->extent();
-        int64_t warps_needed = (n + 127) / 128;
         int64_t max_blocks = (int64_t)sm_count(dev) * 4;
-        int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((warps_needed + kWarps - 1) / kWarps, max_blocks));
-        int64_t per_warp = (n + blocks * kWarps - 1) / (blocks * kWarps);
-        per_warp = (per_warp + 31) / 32 * 32;
+        a.rec_runs = 0;
+        a.nrec_elem = a.rounds_elem = a.q_first = a.nrounds = 0;
+        a.div_rounds = make_div(1);
+        int64_t rsz = 0;
+        const DNode &R = c.nodes()[c.root];
+        if (kRec && rec_shape(c, &rsz)) {
+            const DNode &C = c.nodes()[R.child];
+            const int64_t runs = C.kind == NK_RUN ? 1 : C.count;
+            const int64_t nrec = c.size / rsz;
+            if (nrec * runs == c.nseg) {  // every run of every record is its own segment
+                a.rec_runs = runs;
+                a.nrec_elem = nrec;
+                a.rounds_elem = (nrec + 31) / 32;
+                a.div_rounds = make_div(a.rounds_elem);
+                const int64_t r0 = iov_offset / runs, r1 = (iov_offset + n - 1) / runs;  // records touched
+                const int64_t e0 = r0 / nrec, e1 = r1 / nrec;
+                a.q_first = e0 * a.rounds_elem + (r0 - e0 * nrec) / 32;
+                a.nrounds = e1 * a.rounds_elem + (r1 - e1 * nrec) / 32 - a.q_first + 1;
+            }
+        }
+        int64_t blocks, per_warp;
+        if (a.rec_runs > 0) {
+            // a few rounds per warp, as many warps as there are rounds
+            blocks = std::max<int64_t>(1, std::min<int64_t>((a.nrounds + 4 * kWarps - 1) / (4 * kWarps), max_blocks));
+            per_warp = (a.nrounds + blocks * kWarps - 1) / (blocks * kWarps);
+        } else {
+            int64_t warps_needed = (n + 127) / 128;
+            blocks = std::max<int64_t>(1, std::min<int64_t>((warps_needed + kWarps - 1) / kWarps, max_blocks));
+            per_warp = (n + blocks * kWarps - 1) / (blocks * kWarps);
+            per_warp = (per_warp + 31) / 32 * 32;
+        }
         a.per_warp = per_warp;
         iov_kernel<<<(unsigned)blocks, kThreads, smem, (cudaStream_t)stream>>>(d, a);
         if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;

@@ -385,6 +385,11 @@ def check_record_indexed(nblocks):
     want = np.full(span, SENT, np.uint8)
     o.unpack(ref, 1, want)
     assert np.array_equal(gpu_unpack(t, ref, 1, span, 0), want)
+    if nblocks <= 1 << 16:
+        # the whole segment list, and a window starting inside a record
+        nseg = o.iov_count()
+        iov_check(t, o, 1, 0, nseg)
+        iov_check(t, o, 1, nseg // 3 + 1, nseg // 2)
     # iov queried in chunks of 4096 from random packed byte offsets (each
     # oracle query re-walks the whole type, so fewer at full size)
     nq = 64 if nblocks <= 1 << 16 else 6
