@@ -495,6 +495,60 @@ __global__ void __launch_bounds__(kThreads) at_bytes_fill_kernel(Desc d, int64_t
     }
 }
 
+// Second pass for arrays of short records (the rec_kernel shapes, one
+// element: segment k is run k % runs of record k / runs).  Query q's
+// segments first[q] .. first[q] + actual[q] - 1 lie in rounds of 32 records;
+// task t = q * cpq + c (a warp each, grid-stride) takes rounds c * kRecIovSpan
+// onward of its query, one record per lane, and writes the record's runs that
+// fall inside the query.
+constexpr int64_t kRecIovSpan = 16;  // rounds of 32 records per task
+
+__global__ void __launch_bounds__(kThreads) at_bytes_fill_rec_kernel(Desc d, int64_t nq, int64_t maxlen,
+                                                                     const int64_t *first, const int64_t *actual,
+                                                                     dte_iov *out, const char *base, int64_t runs,
+                                                                     int64_t nrec, FastDiv div_rounds, int64_t cpq)
+{
+    extern __shared__ uint4 smem[];
+    const char *blob;
+    const DNode *nodes;
+    stage_desc(d, smem, blob, nodes);
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+    const DNode &R = nodes[d.root];
+    const DNode &C = nodes[R.child];
+    const int64_t *cpb = C.kind == NK_RUN ? nullptr : arr<int64_t>(blob, C.a_pbytes);
+    const int64_t *cdv = C.kind == NK_RUN ? nullptr : arr<int64_t>(blob, C.a_disp);
+    const Op op = iov_op(d.root, 0);
+    const int64_t rounds_elem = (nrec + 31) / 32;
+    Hint rh{-1, 0};
+    for (int64_t t = warp; t < nq * cpq; t += nwarps) {
+        const int64_t q = t / cpq;
+        const int64_t c = t - q * cpq;
+        const int64_t f = first[q], cnt = actual[q];
+        if (cnt <= 0) continue;
+        const int64_t qa = f / runs / 32, qb = (f + cnt - 1) / runs / 32;  // the query's rounds
+        const int64_t q0 = qa + c * kRecIovSpan;
+        const int64_t q1 = min(q0 + kRecIovSpan, qb + 1);
+        dte_iov *o = out + q * maxlen;
+        for (int64_t rq = q0; rq < q1; rq++) {
+            const RecPlace at = rec_place(op, C, nrec, rounds_elem, div_rounds, rq);
+            const int64_t ud = rec_locate(op, R, C, blob, at, lane, rh);
+            if (lane >= at.nvalid) continue;
+            const int64_t k0 = (at.local0 + lane) * runs - f;
+#pragma unroll 1
+            for (int j = 0; j < (int)runs; j++) {
+                const int64_t k = k0 + j;
+                if (k < 0 || k >= cnt) continue;
+                dte_iov v;
+                v.iov_base = (void *)(base + ud + (cdv ? cdv[j] : 0));
+                v.iov_len = cpb ? cpb[j + 1] - cpb[j] : C.len;
+                o[k] = v;
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // adjoint of the typed float32 pack: gx[src(k)] += gy[k]
 // ---------------------------------------------------------------------------
@@ -1364,6 +1418,28 @@ int dte_type_iov_at_bytes_async(dte_type type, int64_t n, const int64_t *d_offse
             d, n, d_offset, max_iov_len, d_first, d_actual, c.size, c.nseg);
         if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
         if (total > 0) {
+            int64_t rsz = 0;
+            const DNode &R = c.nodes()[c.root];
+            if (kRec && rec_shape(c, &rsz)) {
+                const DNode &C = c.nodes()[R.child];
+                const int64_t runs = C.kind == NK_RUN ? 1 : C.count;
+                const int64_t nrec = c.size / rsz;
+                if (nrec * runs == c.nseg) {
+                    // tasks of kRecIovSpan rounds; a query's records r0 .. r1
+                    // have r1 - r0 <= (max_iov_len - 1) / runs + 1, so they
+                    // span at most (r1 - r0) / 32 + 2 rounds
+                    const int64_t max_rounds = ((max_iov_len - 1) / runs + 1) / 32 + 2;
+                    const int64_t cpq = (max_rounds + kRecIovSpan - 1) / kRecIovSpan;
+                    const int64_t tasks = n * cpq;
+                    const int64_t b2 = std::max<int64_t>(1, std::min<int64_t>((tasks + kWarps - 1) / kWarps, sms * 4));
+                    at_bytes_fill_rec_kernel<<<(unsigned)b2, kThreads, smem, (cudaStream_t)stream>>>(
+                        d, n, max_iov_len, d_first, d_actual, d_iov, (const char *)base, runs, nrec,
+                        make_div((nrec + 31) / 32), cpq);
+                    if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
+                    note_use(type, dev, stream);
+                    return DTE_SUCCESS;
+                }
+            }
             FastDiv dm = make_div(max_iov_len);
             const int64_t warps_needed = (total + 127) / 128;
             const int64_t b2 = std::max<int64_t>(1, std::min<int64_t>((warps_needed + kWarps - 1) / kWarps, sms * 4));

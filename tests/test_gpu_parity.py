@@ -249,9 +249,11 @@ def test_record_block_gather_layouts():
 
 
 def test_list_iov_device_rounds():
-    # large index lists over one shared child: the iov kernels decode rounds
-    # of 32 segments by the warp together; rounds that straddle two elements
-    # (iov) or two queries (at_bytes with 37 segments per query) go lane by lane
+    # large index lists over one shared child (arrays of records): the iov
+    # kernels decode rounds of 32 records by the warp together and write each
+    # record's runs; requests and queries that start or end inside a record,
+    # windows across elements, 37, 64 and 4096 segments per query, and
+    # offsets outside the type
     rng = np.random.default_rng(207)
     s = torch.cuda.current_stream().cuda_stream
     for _ in range(40):
@@ -262,8 +264,8 @@ def test_list_iov_device_rounds():
         first = int(rng.integers(0, max(1, total // 3)))
         iov_check(t, o, count, first, int(rng.integers(1, total - first + 5)))
         sd, sl = o.iov()
-        offs = rng.integers(0, o.size, 24).astype(np.int64)
-        for m in (37, 64):
+        offs = np.concatenate([rng.integers(0, o.size, 24), [-1, o.size]]).astype(np.int64)
+        for m in (37, 64, 4096):
             d_o = torch.from_numpy(offs).to(DEV)
             d_iov = torch.zeros((offs.size * m, 2), dtype=torch.int64, device=DEV)
             d_f = torch.empty_like(d_o)
@@ -273,6 +275,9 @@ def test_list_iov_device_rounds():
             torch.cuda.synchronize()
             f, a, iv = d_f.cpu().numpy(), d_a.cpu().numpy(), d_iov.cpu().numpy()
             for q, b in enumerate(offs):
+                if b < 0 or b >= o.size:
+                    assert (f[q], a[q]) == (-1, 0)
+                    continue
                 k = o.iov_len(int(b))[0]
                 assert f[q] == k and a[q] == min(m, len(sd) - k)
                 got = iv[q * m: q * m + a[q]]
