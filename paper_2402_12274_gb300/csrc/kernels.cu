@@ -118,10 +118,17 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) seg_kernel(Desc d, Op op
 // per-warp shared-memory tiles; a staged unpack keeps two, so that the next
 // round's packed bytes are fetched while the current round is scattered.
 // CTAs per SM the record-major kernels are built for, by direction (records
-// of 2^22 blocks, one box: pack 3.74 / 3.96 / 3.30 TB/s at 4 / 6 / 8, unpack
-// 2.30 / 2.24 / 2.14).
-constexpr int kRecMinBlocksPack = 6;
-constexpr int kRecMinBlocksUnpack = 4;
+// of 2^22 blocks: pack 3.74 / 3.96 / 3.30 TB/s at 4 / 6 / 8 CTAs on one box,
+// 4.12 at 5 against 3.96-3.99 at 6 on another; unpack, with its two tiles,
+// 2.27-2.28 at 4 and 2.22 at 5 or 6).
+#ifndef DTE_REC_MB_PACK
+#define DTE_REC_MB_PACK 5
+#endif
+#ifndef DTE_REC_MB_UNPACK
+#define DTE_REC_MB_UNPACK 4
+#endif
+constexpr int kRecMinBlocksPack = DTE_REC_MB_PACK;
+constexpr int kRecMinBlocksUnpack = DTE_REC_MB_UNPACK;
 template <int W, bool PACK, bool STAGE>
 __global__ void __launch_bounds__(kThreads, PACK ? kRecMinBlocksPack : kRecMinBlocksUnpack)
     rec_kernel(Desc d, Op op, int64_t nrec_elem, int64_t rounds_elem, FastDiv div_rounds, int64_t nrounds, int64_t span)
