@@ -148,6 +148,7 @@ __global__ void __launch_bounds__(kThreads, PACK ? kRecMinBlocksPack : kRecMinBl
     Hint rh{-1, 0};
     for (int64_t q0 = warp * span; q0 < nrounds; q0 += stride) {
         const int64_t q1 = min(q0 + span, nrounds);
+        rh = Hint{-1, 0};  // spans lie far apart: start each with a search by the warp
         if (STAGE && !PACK) {
             rec_unpack_rounds<W>(op, nodes, blob, nrec_elem, rounds_elem, div_rounds, q0, q1, lane, rh, tile);
         } else {
@@ -534,6 +535,7 @@ __global__ void __launch_bounds__(kThreads) at_bytes_fill_rec_kernel(Desc d, int
         const int64_t c = t - q * cpq;
         const int64_t f = first[q], cnt = actual[q];
         if (cnt <= 0) continue;
+        rh = Hint{-1, 0};  // queries land anywhere: a cold search by the warp
         const int64_t qa = f / runs / 32, qb = (f + cnt - 1) / runs / 32;  // the query's rounds
         const int64_t q0 = qa + c * kRecIovSpan;
         const int64_t q1 = min(q0 + kRecIovSpan, qb + 1);
