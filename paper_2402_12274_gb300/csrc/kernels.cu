@@ -105,6 +105,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) seg_kernel(Desc d, Op op
     Hint h{-1, 0}, rh{-1, 0};
     for (int64_t s0 = warp * span; s0 < nsegs; s0 += stride) {
         const int64_t s1 = min(s0 + span, nsegs);
+        rh = Hint{-1, 0};  // spans lie far apart: start each with a search by the warp
         for (int64_t base = s0; base < s1; base += 32)
             seg_round<W, PACK, true, kSegWide>(op, nodes, blob, nseg_elem, div_nseg, seg0 + base, seg0 + s1, lane, h,
                                                rh);
@@ -195,8 +196,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_kernel(const Batch
     for (int64_t j = warp; j < sp.nspans; j += nwarps, p = p + sp.inc >= sp.nspans ? p + sp.inc - sp.nspans : p + sp.inc) {
         const int64_t s0 = p * span;
         const int64_t s1 = min(s0 + span, ntiles);
+        oh = Hint{-1, 0};  // spans lie far apart: find each span's first op by the warp
         for (int64_t t = s0; t < s1; t++) {
-            int64_t i = find_le(tile0, nops, t, oh, 0);
+            int64_t i = warp_find_le_hint(tile0, nops, t, oh, 0, lane);
             const BatchOp *b = ops + i;
             if (i != cur) {
                 h = Hint{-1, 0};
@@ -241,8 +243,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_seg_kernel(const B
     for (int64_t j = warp; j < sp.nspans; j += nwarps, p = p + sp.inc >= sp.nspans ? p + sp.inc - sp.nspans : p + sp.inc) {
         const int64_t s0 = p * span;
         const int64_t s1 = min(s0 + span, ntiles);
+        oh = Hint{-1, 0};  // spans lie far apart: find each span's first op by the warp
         for (int64_t t = s0; t < s1; t++) {
-            int64_t i = find_le(tile0, nops, t, oh, 0);
+            int64_t i = warp_find_le_hint(tile0, nops, t, oh, 0, lane);
             const BatchOp *b = ops + i;
             if (i != cur) {
                 h = Hint{-1, 0};

@@ -444,6 +444,40 @@ __device__ __forceinline__ void warp_step(const Op &op, const DNode *nodes, cons
 // ---------------------------------------------------------------------------
 // segment-major round
 // ---------------------------------------------------------------------------
+// Largest b in [0, n) with a[b] <= x (a sorted, a[0] <= x), found by the warp
+// together: every step the 32 lanes probe 32 evenly spaced entries of the
+// remaining range and one ballot keeps the last probe at or below x, so a
+// table of 2^22 entries takes 5 dependent loads instead of 22.  Warp-uniform
+// arguments; every lane returns the same b.
+__device__ __forceinline__ int64_t warp_find_le(const int64_t *a, int64_t n, int64_t x, int lane)
+{
+    const unsigned FULL = 0xffffffffu;
+    int64_t lo = 0, hi = n;  // a[lo] <= x, and the answer is below hi
+    while (hi - lo > 1) {
+        const int64_t step = (hi - lo + 31) / 32;
+        const int64_t i = lo + lane * step;
+        const unsigned le = __ballot_sync(FULL, i < hi && a[i] <= x);
+        const int k = 31 - __clz(le);  // lane 0 probes lo itself, so le != 0
+        lo += k * step;
+        hi = min(hi, lo + step);
+    }
+    return lo;
+}
+
+// The same lookup with a warp's search position h (warp-uniform): a search
+// by the warp when h is cold (h.node != node), else find_le galloping from h.
+__device__ __forceinline__ int64_t warp_find_le_hint(const int64_t *a, int64_t n, int64_t x, Hint &h, int node,
+                                                     int lane)
+{
+    if (h.node != node) {
+        const int64_t b = warp_find_le(a, n, x, lane);
+        h.node = node;
+        h.b = b;
+        return b;
+    }
+    return find_le(a, n, x, h, node);
+}
+
 // Whether a round can be decoded by shared_list_round: the element's root is
 // a large index list whose entries all repeat one child at one stride (an
 // indexed or hindexed type of any old type) with no segment merging across
@@ -473,7 +507,7 @@ __device__ __forceinline__ void shared_list_round(const Op &op, const DNode *nod
     const DNode &C = nodes[R.child];
     const int64_t *pb = arr<int64_t>(blob, R.a_pbytes);
     const int64_t *dv = arr<int64_t>(blob, R.a_disp);
-    const int64_t b0 = find_le(pb, R.count, fdiv(local0, C.div_nseg) * C.size, rh, op.root);
+    const int64_t b0 = warp_find_le_hint(pb, R.count, fdiv(local0, C.div_nseg) * C.size, rh, op.root, lane);
     const int64_t bj = b0 + lane;
     const int64_t pbj = bj <= R.count ? pb[bj] : INT64_MAX;
     const int64_t dj = bj < R.count ? dv[bj] : 0;
@@ -787,26 +821,6 @@ __device__ __forceinline__ RecPlace rec_place(const Op &op, const DNode &C, int6
     return r;
 }
 
-// Largest b in [0, n) with a[b] <= x (a sorted, a[0] <= x), found by the warp
-// together: every step the 32 lanes probe 32 evenly spaced entries of the
-// remaining range and one ballot keeps the last probe at or below x, so a
-// table of 2^22 entries takes 5 dependent loads instead of 22.  Warp-uniform
-// arguments; every lane returns the same b.
-__device__ __forceinline__ int64_t warp_find_le(const int64_t *a, int64_t n, int64_t x, int lane)
-{
-    const unsigned FULL = 0xffffffffu;
-    int64_t lo = 0, hi = n;  // a[lo] <= x, and the answer is below hi
-    while (hi - lo > 1) {
-        const int64_t step = (hi - lo + 31) / 32;
-        const int64_t i = lo + lane * step;
-        const unsigned le = __ballot_sync(FULL, i < hi && a[i] <= x);
-        const int k = 31 - __clz(le);  // lane 0 probes lo itself, so le != 0
-        lo += k * step;
-        hi = min(hi, lo + step);
-    }
-    return lo;
-}
-
 // User displacement of the lane's record in round `at` (lanes past nvalid
 // get a value that is never used).  Entry b of the root holds records
 // pbytes[b] / size(child) onward (every entry has at least one record and
@@ -820,14 +834,7 @@ __device__ __forceinline__ int64_t rec_locate(const Op &op, const DNode &R, cons
     const unsigned FULL = 0xffffffffu;
     const int64_t *pb = arr<int64_t>(blob, R.a_pbytes);
     const int64_t *dv = arr<int64_t>(blob, R.a_disp);
-    int64_t b0;
-    if (rh.node != op.root) {  // a cold start: search by the warp, then gallop from there
-        b0 = warp_find_le(pb, R.count, at.local0 * C.size, lane);
-        rh.node = op.root;
-        rh.b = b0;
-    } else {
-        b0 = find_le(pb, R.count, at.local0 * C.size, rh, op.root);
-    }
+    const int64_t b0 = warp_find_le_hint(pb, R.count, at.local0 * C.size, rh, op.root, lane);
     const int64_t bj = b0 + lane;
     const int64_t sj = bj <= R.count ? fdiv(pb[bj], C.div_size) : INT64_MAX;  // first record of entry bj
     const int64_t dj = bj < R.count ? dv[bj] : 0;
