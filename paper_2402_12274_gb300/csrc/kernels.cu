@@ -73,6 +73,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) move_kernel(Desc d, Op o
     for (int64_t j = warp; j < sp.nspans; j += nwarps) {
         const int64_t c0 = p * span;
         const int64_t c1 = min(c0 + span, nchunks);
+        if (kSeedHint) seed_root_hint(op, nodes, blob, c0 * 16, h, lane);  // spans lie far apart
         for (int64_t base = c0; base < c1; base += kStepOf<W, WIDE>)
             warp_step<W, PACK, PK16, WIDE>(op, nodes, blob, base, c1, lane, h, scr);
         p += sp.inc;
