@@ -400,10 +400,31 @@ __global__ void __launch_bounds__(kThreads) iov_kernel(Desc d, IovArgs a)
     if (a.actual && blockIdx.x == 0 && threadIdx.x == 0) *a.actual = a.n;
 }
 
+// Packed byte P (0 <= P < size) of one element of an array of short records
+// (the rec_kernel shapes: `runs` runs per record, none merged) -> the index
+// of its segment and the packed offset where that segment starts, without a
+// search: records are contiguous in packed space, so P lies in record
+// P / size(record), in the last run of it that starts at or before P.
+__device__ __forceinline__ void rec_pos(const DNode *nodes, const char *blob, int root, int64_t runs, int64_t P,
+                                        int64_t &k, int64_t &start)
+{
+    const DNode &C = nodes[nodes[root].child];
+    const int64_t r = fdiv(P, C.div_size);
+    const int64_t o = P - r * C.size;
+    int64_t j = 0, pj = 0;
+    if (C.kind != NK_RUN) {
+        const int64_t *cpb = arr<int64_t>(blob, C.a_pbytes);
+        while (j + 1 < runs && cpb[j + 1] <= o) j++;
+        pj = cpb[j];
+    }
+    k = r * runs + j;
+    start = r * C.size + pj;
+}
+
 // §3.1 MPIX_Type_iov_len for a batch of budgets
 __global__ void __launch_bounds__(kThreads) iov_len_kernel(Desc d, int64_t nq, const int64_t *budget,
                                                            int64_t *out_len, int64_t *out_bytes, int64_t size,
-                                                           int64_t nseg)
+                                                           int64_t nseg, int64_t rec_runs)
 {
     extern __shared__ uint4 smem[];
     const char *blob;
@@ -419,6 +440,8 @@ __global__ void __launch_bounds__(kThreads) iov_len_kernel(Desc d, int64_t nq, c
         } else if (B == -1 || B >= size) {
             k = nseg;
             st = size;
+        } else if (rec_runs > 0) {
+            rec_pos(nodes, blob, d.root, rec_runs, B, k, st);
         } else {
             decode_pos(nodes, blob, d.root, B, k, st);
         }
@@ -430,7 +453,8 @@ __global__ void __launch_bounds__(kThreads) iov_len_kernel(Desc d, int64_t nq, c
 // byte offset -> first segment index and count (first pass of iov_at_bytes)
 __global__ void __launch_bounds__(kThreads) at_bytes_first_kernel(Desc d, int64_t nq, const int64_t *off,
                                                                   int64_t maxlen, int64_t *first,
-                                                                  int64_t *actual, int64_t size, int64_t nseg)
+                                                                  int64_t *actual, int64_t size, int64_t nseg,
+                                                                  int64_t rec_runs)
 {
     extern __shared__ uint4 smem[];
     const char *blob;
@@ -445,7 +469,8 @@ __global__ void __launch_bounds__(kThreads) at_bytes_first_kernel(Desc d, int64_
             continue;
         }
         int64_t k, st;
-        decode_pos(nodes, blob, d.root, B, k, st);
+        if (rec_runs > 0) rec_pos(nodes, blob, d.root, rec_runs, B, k, st);
+        else decode_pos(nodes, blob, d.root, B, k, st);
         first[q] = k;
         actual[q] = min(maxlen, nseg - k);
     }
@@ -1301,6 +1326,17 @@ int dte_unpack_batch_enqueue(int64_t nops, const dte_op *ops, dte_stream_t strea
     return batch_once(DTE_BATCH_UNPACK, nops, ops, stream);
 }
 
+// Runs per record when a type is an array of short records whose every run
+// is its own segment (the shapes the record-major kernels take), else 0.
+static int64_t rec_runs_of(const Committed &c)
+{
+    int64_t rsz = 0;
+    if (!kRec || !rec_shape(c, &rsz)) return 0;
+    const DNode &C = c.nodes()[c.nodes()[c.root].child];
+    const int64_t runs = C.kind == NK_RUN ? 1 : C.count;
+    return (c.size / rsz) * runs == c.nseg ? runs : 0;
+}
+
 int dte_type_iov_async(dte_type type, int64_t count, int64_t iov_offset, dte_iov *d_iov, int64_t max_iov_len,
                        int64_t *d_actual_iov_len, const void *base, dte_stream_t stream)
 {
@@ -1338,22 +1374,16 @@ int dte_type_iov_async(dte_type type, int64_t count, int64_t iov_offset, dte_iov
         a.rec_runs = 0;
         a.nrec_elem = a.rounds_elem = a.q_first = a.nrounds = 0;
         a.div_rounds = make_div(1);
-        int64_t rsz = 0;
-        const DNode &R = c.nodes()[c.root];
-        if (kRec && rec_shape(c, &rsz)) {
-            const DNode &C = c.nodes()[R.child];
-            const int64_t runs = C.kind == NK_RUN ? 1 : C.count;
-            const int64_t nrec = c.size / rsz;
-            if (nrec * runs == c.nseg) {  // every run of every record is its own segment
-                a.rec_runs = runs;
-                a.nrec_elem = nrec;
-                a.rounds_elem = (nrec + 31) / 32;
-                a.div_rounds = make_div(a.rounds_elem);
-                const int64_t r0 = iov_offset / runs, r1 = (iov_offset + n - 1) / runs;  // records touched
-                const int64_t e0 = r0 / nrec, e1 = r1 / nrec;
-                a.q_first = e0 * a.rounds_elem + (r0 - e0 * nrec) / 32;
-                a.nrounds = e1 * a.rounds_elem + (r1 - e1 * nrec) / 32 - a.q_first + 1;
-            }
+        if (const int64_t runs = rec_runs_of(c)) {
+            const int64_t nrec = c.nseg / runs;
+            a.rec_runs = runs;
+            a.nrec_elem = nrec;
+            a.rounds_elem = (nrec + 31) / 32;
+            a.div_rounds = make_div(a.rounds_elem);
+            const int64_t r0 = iov_offset / runs, r1 = (iov_offset + n - 1) / runs;  // records touched
+            const int64_t e0 = r0 / nrec, e1 = r1 / nrec;
+            a.q_first = e0 * a.rounds_elem + (r0 - e0 * nrec) / 32;
+            a.nrounds = e1 * a.rounds_elem + (r1 - e1 * nrec) / 32 - a.q_first + 1;
         }
         int64_t blocks, per_warp;
         if (a.rec_runs > 0) {
@@ -1395,7 +1425,8 @@ int dte_type_iov_len_async(dte_type type, int64_t n, const int64_t *d_budget, in
         Desc d = make_desc(c, blob, &smem);
         int64_t blocks = std::min<int64_t>((n + kThreads - 1) / kThreads, (int64_t)sm_count(dev) * 4);
         iov_len_kernel<<<(unsigned)blocks, kThreads, smem, (cudaStream_t)stream>>>(d, n, d_budget, d_iov_len,
-                                                                                  d_iov_bytes, c.size, c.nseg);
+                                                                                  d_iov_bytes, c.size, c.nseg,
+                                                                                  rec_runs_of(c));
         if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
         note_use(type, dev, stream);
         return DTE_SUCCESS;
@@ -1428,30 +1459,24 @@ int dte_type_iov_at_bytes_async(dte_type type, int64_t n, const int64_t *d_offse
         int64_t sms = sm_count(dev);
         int64_t b1 = std::min<int64_t>((n + kThreads - 1) / kThreads, sms * 4);
         at_bytes_first_kernel<<<(unsigned)b1, kThreads, smem, (cudaStream_t)stream>>>(
-            d, n, d_offset, max_iov_len, d_first, d_actual, c.size, c.nseg);
+            d, n, d_offset, max_iov_len, d_first, d_actual, c.size, c.nseg, rec_runs_of(c));
         if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
         if (total > 0) {
-            int64_t rsz = 0;
-            const DNode &R = c.nodes()[c.root];
-            if (kRec && rec_shape(c, &rsz)) {
-                const DNode &C = c.nodes()[R.child];
-                const int64_t runs = C.kind == NK_RUN ? 1 : C.count;
-                const int64_t nrec = c.size / rsz;
-                if (nrec * runs == c.nseg) {
-                    // tasks of kRecIovSpan rounds; a query's records r0 .. r1
-                    // have r1 - r0 <= (max_iov_len - 1) / runs + 1, so they
-                    // span at most (r1 - r0) / 32 + 2 rounds
-                    const int64_t max_rounds = ((max_iov_len - 1) / runs + 1) / 32 + 2;
-                    const int64_t cpq = (max_rounds + kRecIovSpan - 1) / kRecIovSpan;
-                    const int64_t tasks = n * cpq;
-                    const int64_t b2 = std::max<int64_t>(1, std::min<int64_t>((tasks + kWarps - 1) / kWarps, sms * 4));
-                    at_bytes_fill_rec_kernel<<<(unsigned)b2, kThreads, smem, (cudaStream_t)stream>>>(
-                        d, n, max_iov_len, d_first, d_actual, d_iov, (const char *)base, runs, nrec,
-                        make_div((nrec + 31) / 32), cpq);
-                    if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
-                    note_use(type, dev, stream);
-                    return DTE_SUCCESS;
-                }
+            if (const int64_t runs = rec_runs_of(c)) {
+                const int64_t nrec = c.nseg / runs;
+                // tasks of kRecIovSpan rounds; a query's records r0 .. r1
+                // have r1 - r0 <= (max_iov_len - 1) / runs + 1, so they
+                // span at most (r1 - r0) / 32 + 2 rounds
+                const int64_t max_rounds = ((max_iov_len - 1) / runs + 1) / 32 + 2;
+                const int64_t cpq = (max_rounds + kRecIovSpan - 1) / kRecIovSpan;
+                const int64_t tasks = n * cpq;
+                const int64_t b2 = std::max<int64_t>(1, std::min<int64_t>((tasks + kWarps - 1) / kWarps, sms * 4));
+                at_bytes_fill_rec_kernel<<<(unsigned)b2, kThreads, smem, (cudaStream_t)stream>>>(
+                    d, n, max_iov_len, d_first, d_actual, d_iov, (const char *)base, runs, nrec,
+                    make_div((nrec + 31) / 32), cpq);
+                if (cudaGetLastError() != cudaSuccess) return DTE_ERR_CUDA;
+                note_use(type, dev, stream);
+                return DTE_SUCCESS;
             }
             FastDiv dm = make_div(max_iov_len);
             const int64_t warps_needed = (total + 127) / 128;

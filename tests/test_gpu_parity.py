@@ -251,9 +251,10 @@ def test_record_block_gather_layouts():
 def test_list_iov_device_rounds():
     # large index lists over one shared child (arrays of records): the iov
     # kernels decode rounds of 32 records by the warp together and write each
-    # record's runs; requests and queries that start or end inside a record,
-    # windows across elements, 37, 64 and 4096 segments per query, and
-    # offsets outside the type
+    # record's runs, and map byte offsets and budgets to segments directly;
+    # requests and queries that start or end inside a record, windows across
+    # elements, 37, 64 and 4096 segments per query, and offsets and budgets
+    # outside the type
     rng = np.random.default_rng(207)
     s = torch.cuda.current_stream().cuda_stream
     for _ in range(40):
@@ -264,6 +265,14 @@ def test_list_iov_device_rounds():
         first = int(rng.integers(0, max(1, total // 3)))
         iov_check(t, o, count, first, int(rng.integers(1, total - first + 5)))
         sd, sl = o.iov()
+        budgets = np.unique(np.concatenate([rng.integers(-3, o.size + 4, 48), [-1, 0, o.size]])).astype(np.int64)
+        d_b = torch.from_numpy(budgets).to(DEV)
+        d_n = torch.empty_like(d_b)
+        d_y = torch.empty_like(d_b)
+        dte.dte_type_iov_len_async(t.h, budgets.size, d_b.data_ptr(), d_n.data_ptr(), d_y.data_ptr(), s)
+        torch.cuda.synchronize()
+        for b, nn, y in zip(budgets, d_n.cpu().numpy(), d_y.cpu().numpy()):
+            assert (nn, y) == ((-1, -1) if b < -1 else o.iov_len(int(b))), (spec, b)
         offs = np.concatenate([rng.integers(0, o.size, 24), [-1, o.size]]).astype(np.int64)
         for m in (37, 64, 4096):
             d_o = torch.from_numpy(offs).to(DEV)
