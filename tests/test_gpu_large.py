@@ -1,6 +1,6 @@
-"""Moves past 32-bit offsets: a packed stream longer than 4 GiB (chunk-major
-and bulk-copy kernels, a range window across 2^32, a batch), and a
-segment-major move of more than 2^31 segments.
+"""Moves past 32-bit offsets: a packed stream longer than 4 GiB (chunk-major,
+bulk-copy and record-major kernels, a range window across 2^32, a batch),
+and a segment-major move of more than 2^31 segments.
 
 The oracle walks every typemap entry, so it is run on one element and the
 full-size result is checked through a property of pack, which is a byte
@@ -131,3 +131,17 @@ def test_more_than_2_31_segments_segment_major():
     t, o = both(spec)
     assert o.iov_count() == 33 and count * 33 > (1 << 31)
     big_round_trip(spec, count, rng)
+
+
+def test_records_beyond_4GiB_record_major():
+    # an array of records under an index list of 34 entries (irregular
+    # displacements, so it stays a list), each two 4-byte records 8 bytes
+    # apart: the record-major kernels with their staged tiles (272 packed
+    # bytes per element, a multiple of 16); 15,794,419 elements give 4.3 GB
+    # packed and 10.6 GB of element span
+    rng = np.random.default_rng(306)
+    disp = np.concatenate([[0], np.cumsum(np.where(np.arange(33) % 2, 3, 2))]).astype(np.int64)
+    spec = ("indexed", np.full(34, 2, np.int64), disp, ("resized", 0, 8, ("basic", "int32")))
+    t, o = both(spec)
+    assert (o.size, o.extent) == (272, 672)
+    big_round_trip(spec, (1 << 32) // o.size + 4099, rng)
