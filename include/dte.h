@@ -491,7 +491,7 @@ typedef struct dte_server_config {
                                     requests; a larger request is admitted alone.  0 = the
                                     default: DTE_SERVE_MAX_INFLIGHT_BYTES from the environment
                                     (a positive integer) if set, else 8 GiB */
-    int32_t ctas_per_sm;         /* persistent CTAs per SM, 1 or 2 (default 2) */
+    int32_t ctas_per_sm;         /* persistent CTAs per SM, 1 to 4 (default 4) */
     int32_t span_tiles;          /* fewest tiles (1-2 KiB, or 32-segment rounds) a warp claims at once,
                                     1..65536; claims grow to 64 while many published tiles are
                                     unclaimed (default 8) */
