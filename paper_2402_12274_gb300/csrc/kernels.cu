@@ -24,9 +24,14 @@
 //    load and one 16-byte store.  Smaller W assembles the chunk run by run
 //    from W-byte words.
 //  * Short runs under large index tables move segment-major (seg_kernel);
-//    long runs with W = 16 in moves large enough to give every warp of the
-//    bulk grid several 16 KiB tiles move by TMA bulk copies (bulk_kernel,
-//    bulk.cuh).
+//    whole moves of arrays of short records (an index list over one struct
+//    of a few runs) move record-major, a record per lane with the packed
+//    side staged in shared memory (rec_kernel); long runs with W = 16 in
+//    moves large enough to give every warp of the bulk grid several 16 KiB
+//    tiles move by TMA bulk copies (bulk_kernel, bulk.cuh).
+//  * A warp whose search position is far from its target (a new span of the
+//    spread or strided work order, a new query) searches by the warp: 32
+//    probes a step (warp_find_le), then gallops from there.
 //  * Bytes are moved verbatim through integer registers: no value is ever
 //    converted, so NaN payloads survive.
 //  * Batches: many independent operations (different types, buffers and
