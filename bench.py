@@ -852,7 +852,7 @@ def run_config_autograd(args):
                                             "backward_us": round(tb * 1e6, 1), "entries": t.size // 4})
 
 
-def serve_measure(nreq: int, rhos=(0.5, 0.8, 0.95), seed: int = 5, ctas_per_sm: int = 4, span_tiles: int = 8):
+def serve_measure(nreq: int, rhos=(0.5, 0.8, 0.95), seed: int = 5, ctas_per_sm: int = 4, span_tiles: int = 4):
     """Request loop under Poisson arrivals: pack/unpack requests (50/50) of
     layouts from the batch generator with sizes log-uniform 1 KiB - 64 MiB,
     admission cap 8 GiB.  The service rate mu is measured first (all requests

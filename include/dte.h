@@ -494,7 +494,7 @@ typedef struct dte_server_config {
     int32_t ctas_per_sm;         /* persistent CTAs per SM, 1 to 4 (default 4) */
     int32_t span_tiles;          /* fewest tiles (1-2 KiB, or 32-segment rounds) a warp claims at once,
                                     1..65536; claims grow to 64 while many published tiles are
-                                    unclaimed (default 8) */
+                                    unclaimed (default 4) */
     int64_t idle_exit_us;        /* empty-poll budget before the loop leaves (default 50000) */
 } dte_server_config;
 

@@ -457,7 +457,7 @@ def dte_pack_adjoint_f32_enqueue(gy: int, count: int, t: int, gx: int, stream: i
 
 
 def dte_server_create(ring_slots: int = 1024, max_inflight_bytes: int = 0, ctas_per_sm: int = 4,
-                      span_tiles: int = 8, idle_exit_us: int = 50000) -> int:
+                      span_tiles: int = 4, idle_exit_us: int = 50000) -> int:
     cfg = dte_server_config(ring_slots, max_inflight_bytes, ctas_per_sm, span_tiles, idle_exit_us)
     out = C.c_void_p()
     _ck(lib.dte_server_create(C.byref(cfg), C.byref(out)), "dte_server_create")
